@@ -1,0 +1,463 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: printed values, closed forms
+(Fourier symbols, tanh profile, Laplace law, linear Cahn-Hilliard and shear-wave decay,
+hydrostatics), exact moment algebra, invariants (conservation, lattice symmetries) and a
+brute-force finite-difference check of the mass defect (Eq. 5).  A dropped term, a wrong sign,
+index or weight anywhere in the oracle breaks at least one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+CS2 = 1.0 / 3.0
+EX = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+EY = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def params(**kw):
+    phys = W.Physical(**{k: v for k, v in kw.items() if k in W.Physical.__dataclass_fields__})
+    return oracle.params_from_physical(phys)
+
+
+# ----------------------------------------------------------------- printed values
+
+
+def test_weights_match_paper():
+    """g^eq at u = 0 is w_a p: the printed D2Q9 weights (text after Eq. 5)."""
+    gd = golden()
+    P = params(sigma=0.01, W=4.0)
+    feq, geq, G = oracle.node_equilibria(P, 0.3, 0.0, 0.7, 1.0, 0.0, 0.0)
+    want = [gd["w0"]] + [gd["w1_4"]] * 4 + [gd["w5_8"]] * 4
+    np.testing.assert_allclose(geq, want, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(G, want, rtol=0, atol=1e-15)
+
+
+def test_paper_dimensionless_groups():
+    """The experiments' printed groups are consistent with the workload recipes (We, Re, Eo)."""
+    gd = golden()
+    assert gd["splash_U"] ** 2 * gd["splash_D"] / gd["splash_sigma"] == pytest.approx(gd["splash_We"])
+    assert gd["splash_U"] * gd["splash_D"] / gd["splash_nu_low"] == pytest.approx(gd["splash_Re_low"])
+    assert gd["splash_U"] * gd["splash_D"] / gd["splash_nu_high"] == pytest.approx(gd["splash_Re_high"])
+    w = W.paper_falling_droplet(steps=0)
+    Eo = w.phys.gravity * (w.phys.rho_A - w.phys.rho_B) * (2 * w.meta["R"]) ** 2 / w.phys.sigma
+    assert Eo == pytest.approx(gd["fall_Eo"])
+    c3 = W.splash()
+    assert c3.phys.rho_A * c3.meta["U"] ** 2 * 200.0 / c3.phys.sigma == pytest.approx(8000.0)
+
+
+# ----------------------------------------------------------------- exact moment algebra
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_omega_moments(seed):
+    """omega_a(u) (text after Eq. 5): sum = 1, first moment u, second moment cs2 I + u u."""
+    rng = np.random.default_rng(seed)
+    ux, uy = rng.uniform(-0.1, 0.1, 2)
+    P = params(sigma=0.01, W=4.0)
+    _, _, G = oracle.node_equilibria(P, 0.0, 0.0, 1.0, 0.0, ux, uy)
+    assert G.sum() == pytest.approx(1.0, abs=1e-15)
+    assert (EX * G).sum() == pytest.approx(ux, abs=1e-15)
+    assert (EY * G).sum() == pytest.approx(uy, abs=1e-15)
+    assert (EX * EX * G).sum() == pytest.approx(CS2 + ux * ux, abs=1e-15)
+    assert (EY * EY * G).sum() == pytest.approx(CS2 + uy * uy, abs=1e-15)
+    assert (EX * EY * G).sum() == pytest.approx(ux * uy, abs=1e-15)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_equilibrium_moments(seed):
+    """g^eq = cs2 f^eq + psi w (text after Eq. 5): sum p, first moment rho cs2 u,
+    second moment cs2 (p I + rho u u).  f^eq (the Cahn-Hilliard equilibrium): sum phi,
+    first moment phi u, second moment Gamma_f mu I + phi u u with Gamma_f (tau_f - 1/2) = theta_M."""
+    rng = np.random.default_rng(100 + seed)
+    P = params(sigma=0.02, W=3.0, theta_M=rng.uniform(0.05, 0.5), tau_f=rng.uniform(0.6, 1.5))
+    phi, mu, rho, p, ux, uy = rng.uniform(-1, 1), rng.uniform(-1e-2, 1e-2), rng.uniform(0.1, 2), \
+        rng.uniform(-1e-3, 1e-3), *rng.uniform(-0.1, 0.1, 2)
+    feq, geq, _ = oracle.node_equilibria(P, phi, mu, rho, p, ux, uy)
+    Gf = P.theta_M / (P.tau_f - 0.5)
+    tol = 1e-14
+    assert geq.sum() == pytest.approx(p, abs=tol)
+    assert (EX * geq).sum() == pytest.approx(rho * CS2 * ux, abs=tol)
+    assert (EY * geq).sum() == pytest.approx(rho * CS2 * uy, abs=tol)
+    assert (EX * EX * geq).sum() == pytest.approx(CS2 * (p + rho * ux * ux), abs=tol)
+    assert (EX * EY * geq).sum() == pytest.approx(CS2 * rho * ux * uy, abs=tol)
+    assert feq.sum() == pytest.approx(phi, abs=tol)
+    assert (EX * feq).sum() == pytest.approx(phi * ux, abs=tol)
+    assert (EY * feq).sum() == pytest.approx(phi * uy, abs=tol)
+    assert (EX * EX * feq).sum() == pytest.approx(Gf * mu + phi * ux * ux, abs=tol)
+    assert (EY * EY * feq).sum() == pytest.approx(Gf * mu + phi * uy * uy, abs=tol)
+    assert (EX * EY * feq).sum() == pytest.approx(phi * ux * uy, abs=tol)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_forcing_moments(seed):
+    """S_a = (e_a - u).K of Eq. 8: sum = -u.grad(psi), first moment cs2 F."""
+    rng = np.random.default_rng(200 + seed)
+    ux, uy, Fx, Fy, dx, dy = rng.uniform(-0.1, 0.1, 6)
+    S = oracle.node_forcing(ux, uy, Fx, Fy, dx, dy)
+    assert S.sum() == pytest.approx(-(ux * dx + uy * dy), abs=1e-15)
+    assert (EX * S).sum() == pytest.approx(CS2 * Fx, abs=1e-15)
+    assert (EY * S).sum() == pytest.approx(CS2 * Fy, abs=1e-15)
+
+
+@pytest.mark.parametrize("remove_Fa", [0, 1])
+def test_collision_momentum_impulse(remove_Fa):
+    """The collision adds the full force impulse: sum_a e_a (gbar*_a - gbar_a) = cs2 F at every
+    node, F = F_s + G (+ u s with F_a removed).  This holds only if u is taken from the first
+    moment of gbar with the half-force shift (and the (rho - s/2) denominator when the force
+    includes u s), so it pins the velocity formula of the second-order scheme."""
+    w = W.random_small(24, 20, seed=7, bc_y=W.WALL, gravity=1e-4, remove_Fa=remove_Fa, ratio=5.0)
+    s = oracle.Sim.from_workload(w)
+    s.step(5)
+    f, g = s.get_state()
+    m = s.moments()
+    fsx, fsy, sdef = s.field(oracle.FSX), s.field(oracle.FSY), s.field(oracle.S)
+    fst, gst = s.collide()
+    Fx = fsx + (m["ux"] * sdef if remove_Fa else 0.0)
+    Fy = fsy - m["rho"] * w.phys.gravity + (m["uy"] * sdef if remove_Fa else 0.0)
+    imp_x = np.tensordot(EX, gst - g, axes=1)
+    imp_y = np.tensordot(EY, gst - g, axes=1)
+    np.testing.assert_allclose(imp_x, CS2 * Fx, atol=1e-15)
+    np.testing.assert_allclose(imp_y, CS2 * Fy, atol=1e-15)
+    # the f collision conserves phi locally
+    np.testing.assert_allclose(fst.sum(0), f.sum(0), atol=1e-14)
+
+
+# ----------------------------------------------------------------- stencils
+
+
+@pytest.mark.parametrize("kx,ky", [(1, 0), (0, 2), (3, 1), (5, 7), (8, 8)])
+def test_isotropic_stencils_fourier(kx, ky):
+    """Closed-form symbols of the isotropic central differences on a periodic grid:
+    lap -> (8 (cos kx + cos ky) + 4 cos kx cos ky - 20) / 6,
+    d/dx -> i sin kx (4 + 2 cos ky) / 6."""
+    n = 32
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    a, b = 2 * np.pi * kx / n, 2 * np.pi * ky / n
+    phase = a * x + b * y
+    f = np.cos(phase)
+    lam = (8 * (np.cos(a) + np.cos(b)) + 4 * np.cos(a) * np.cos(b) - 20) / 6
+    np.testing.assert_allclose(oracle.lap_iso(f), lam * f, atol=1e-13)
+    gx, gy = oracle.grad_iso(f)
+    np.testing.assert_allclose(gx, -np.sin(phase) * np.sin(a) * (4 + 2 * np.cos(b)) / 6, atol=1e-13)
+    np.testing.assert_allclose(gy, -np.sin(phase) * np.sin(b) * (4 + 2 * np.cos(a)) / 6, atol=1e-13)
+
+
+def test_isotropic_stencils_exact_on_polynomials():
+    """Central isotropic stencils are exact on quadratics (Laplacian) and cubics (gradient)
+    away from the boundary."""
+    n = 16
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    q = 0.3 * x * x - 0.7 * x * y + 1.1 * y * y + 0.2 * x - 0.5
+    inner = (slice(1, -1), slice(1, -1))
+    np.testing.assert_allclose(oracle.lap_iso(q, W.WALL, W.WALL)[inner], 2 * 0.3 + 2 * 1.1, atol=1e-11)
+    c = x ** 2 * y + 0.5 * x
+    gx, gy = oracle.grad_iso(c, W.WALL, W.WALL)
+    # d/dx of x^2 y + x/2 is 2 x y + 1/2; the stencil adds (dx^2/6) d3/dx3 (=0) and
+    # the diagonal terms' (1/6) d3/dxdy2 (=0) -> exact
+    np.testing.assert_allclose(gx[inner], (2 * x * y + 0.5)[inner], atol=1e-10)
+    # d/dy of x^2 y is x^2; diagonal stencil adds (1/6) d3/dx2dy = 1/3
+    np.testing.assert_allclose(gy[inner], (x * x + 1.0 / 3.0)[inner], atol=1e-10)
+
+
+def test_wall_mirror_zero_normal_gradient():
+    """At a wall the stencils see mirrored ghosts: a field that is even about the wall plane
+    (half a cell outside the first row) has zero normal gradient there."""
+    n = 12
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    f = np.cos(2 * np.pi * x / n) * np.cos(np.pi * (y + 0.5) / n)   # even about y=-1/2, y=n-1/2
+    gx, gy = oracle.grad_iso(f, W.PERIODIC, W.WALL)
+    gyp, _ = oracle.grad_iso(np.vstack([f[::-1], f, f[::-1]]).T, W.PERIODIC, W.PERIODIC)
+    # compare with the same field extended by explicit reflection on a periodic 3n strip
+    ext = np.vstack([f[::-1], f, f[::-1]])
+    gx_e, gy_e = oracle.grad_iso(ext, W.PERIODIC, W.PERIODIC)
+    np.testing.assert_allclose(gy, gy_e[n:2 * n], atol=1e-14)
+    np.testing.assert_allclose(oracle.lap_iso(f, W.PERIODIC, W.WALL),
+                               oracle.lap_iso(ext, W.PERIODIC, W.PERIODIC)[n:2 * n], atol=1e-14)
+
+
+# ----------------------------------------------------------------- streaming
+
+
+@pytest.mark.parametrize("bc_x,bc_y", [(0, 0), (0, 1), (1, 1)])
+def test_streaming_brute_force(bc_x, bc_y):
+    """Every population moves one link along e_a; links leaving through a wall come back
+    reversed at the same cell; periodic links wrap.  Checked cell by cell on a tiny grid."""
+    nx, ny = 5, 4
+    rng = np.random.default_rng(3)
+    pop = rng.standard_normal((9, ny, nx))
+    out = oracle.stream(pop, bc_x, bc_y)
+    opp = [0, 3, 4, 1, 2, 7, 8, 5, 6]
+    for a in range(9):
+        assert EX[opp[a]] == -EX[a] and EY[opp[a]] == -EY[a]
+        for y in range(ny):
+            for x in range(nx):
+                xd, yd = x + EX[a], y + EY[a]
+                out_x = not (0 <= xd < nx)
+                out_y = not (0 <= yd < ny)
+                if (out_x and bc_x == 1) or (out_y and bc_y == 1):
+                    assert out[opp[a], y, x] == pop[a, y, x]
+                else:
+                    assert out[a, yd % ny, xd % nx] == pop[a, y, x]
+    assert np.isfinite(out).all()
+
+
+# ----------------------------------------------------------------- invariants
+
+
+@pytest.mark.parametrize("bc_y,remove_Fa", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_total_phi_conserved(bc_y, remove_Fa):
+    """Eq. 5 integrated: total phi is constant on periodic or walled boxes (BGK conserves
+    sum_a f_a at each node and streaming/bounce-back only moves populations)."""
+    w = W.random_small(33, 17, seed=11, bc_y=bc_y, remove_Fa=remove_Fa, gravity=1e-5 * bc_y)
+    s = oracle.Sim.from_workload(w)
+    s0 = s.moments()["phi"].sum()
+    for _ in range(10):
+        s.step(20)
+        assert abs(s.moments()["phi"].sum() - s0) <= 1e-12 * w.cells
+
+
+def test_transpose_symmetry():
+    """D2Q9 and the isotropic stencils are symmetric under x <-> y: a transpose-symmetric state
+    on a square periodic box stays transpose-symmetric, with u_x(x,y) = u_y(y,x)."""
+    n = 40
+    phi = np.maximum(W.droplet_phi(n, n, 18.0, 22.0, 8.0, 4.0), W.droplet_phi(n, n, 22.0, 18.0, 8.0, 4.0))
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    ux = 0.01 * np.sin(2 * np.pi * y / n) * np.cos(2 * np.pi * x / n)
+    uy = ux.T.copy()
+    phi = 0.5 * (phi + phi.T)
+    for rf in (0, 1):
+        phys = W.Physical(sigma=0.01, W=4.0, rho_B=0.2, remove_Fa=rf)
+        s = oracle.Sim.from_workload(W.make("t", n, n, phys, 0, phi, ux, uy))
+        s.step(60)
+        m = s.moments()
+        np.testing.assert_allclose(m["phi"], m["phi"].T, atol=1e-12)
+        np.testing.assert_allclose(m["p"], m["p"].T, atol=1e-14)
+        np.testing.assert_allclose(m["ux"], m["uy"].T, atol=1e-14)
+
+
+def test_mirror_symmetry_with_walls_and_gravity():
+    """Reflection x -> nx-1-x maps the walled, gravity-driven problem onto itself:
+    phi and p are even, u_x odd."""
+    nx, ny = 30, 24
+    phi = W.droplet_phi(nx, ny, (nx - 1) / 2, 14.0, 6.0, 4.0, periodic_y=False)
+    phi = 0.5 * (phi + phi[:, ::-1])
+    phys = W.Physical(sigma=0.01, W=4.0, rho_B=0.1, gravity=1e-4, bc_y=W.WALL, remove_Fa=1)
+    s = oracle.Sim.from_workload(W.make("m", nx, ny, phys, 0, phi))
+    s.step(80)
+    m = s.moments()
+    np.testing.assert_allclose(m["phi"], m["phi"][:, ::-1], atol=1e-12)
+    np.testing.assert_allclose(m["p"], m["p"][:, ::-1], atol=1e-14)
+    np.testing.assert_allclose(m["ux"], -m["ux"][:, ::-1], atol=1e-14)
+    assert np.abs(m["uy"]).max() > 1e-6
+
+
+def test_density_is_affine_in_phi():
+    """Eq. 4 (second form): rho(+phi*) = rho_A, rho(-phi*) = rho_B, affine in between."""
+    nx, ny = 8, 6
+    phi = np.linspace(-1, 1, nx * ny).reshape(ny, nx)
+    phys = W.Physical(sigma=1e-12, W=4.0, rho_A=2.0, rho_B=0.25, theta_M=0.0)
+    s = oracle.Sim.from_workload(W.make("r", nx, ny, phys, 0, phi))
+    rho = s.moments()["rho"]
+    np.testing.assert_allclose(rho, 0.25 + (phi + 1) / 2 * 1.75, atol=1e-9)
+
+
+def test_original_and_corrected_identical_without_mass_defect():
+    """-F_a = u s: a uniform phase on a periodic box under gravity accelerates (u != 0) but keeps
+    s = 0 exactly, so the two schemes are bit-identical; they differ once an interface moves."""
+    nx, ny = 12, 16
+    phys0 = W.Physical(sigma=0.01, W=4.0, rho_B=0.1, gravity=1e-4)
+    phys1 = W.Physical(**{**phys0.__dict__, "remove_Fa": 1})
+    phi = np.full((ny, nx), 0.6)
+    a = oracle.Sim.from_workload(W.make("a", nx, ny, phys0, 0, phi))
+    b = oracle.Sim.from_workload(W.make("b", nx, ny, phys1, 0, phi))
+    a.step(50)
+    b.step(50)
+    fa, ga = a.get_state()
+    fb, gb = b.get_state()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert abs(a.moments()["uy"]).min() > 1e-4
+    w = W.random_small(20, 20, seed=5, u_amp=0.02)
+    c0 = oracle.run(w, steps=50, remove_Fa=0).moments()
+    c1 = oracle.run(w, steps=50, remove_Fa=1).moments()
+    assert np.abs(c0["ux"] - c1["ux"]).max() > 1e-9
+
+
+# ----------------------------------------------------------------- closed forms
+
+
+def test_params_from_sigma_W_closed_form():
+    """Planar equilibrium of Eq. 1: W = sqrt(2 kappa/beta)/phi*, sigma = (4/3) sqrt(2 kappa beta) phi*^3."""
+    for sigma, Wd, ps in ((0.01, 4.0, 1.0), (0.005, 5.0, 1.0), (0.002, 3.0, 0.5)):
+        beta, kappa = oracle.params_from_sigma_W(sigma, Wd, ps)
+        assert math.sqrt(2 * kappa / beta) / ps == pytest.approx(Wd, rel=1e-14)
+        assert 4.0 / 3.0 * math.sqrt(2 * kappa * beta) * ps ** 3 == pytest.approx(sigma, rel=1e-14)
+
+
+def test_planar_interface_width_and_tension():
+    """A planar liquid slab relaxes to the tanh profile of width W with surface tension
+    sigma = kappa * integral (dphi/dx)^2 (closed form from Eq. 1), within 3 %."""
+    from scipy.optimize import curve_fit
+    nx, ny, Wd, sigma = 160, 4, 8.0, 0.01
+    phys = W.Physical(sigma=sigma, W=Wd, rho_B=0.1, theta_M=0.3)
+    phi0 = W.planar_slab_phi(nx, ny, 40, 120, 0.875 * Wd)    # start too sharp
+    s = oracle.Sim.from_workload(W.make("slab", nx, ny, phys, 0, phi0))
+    s.step(25000)
+    phi = s.moments()["phi"][0]
+    xs = np.arange(nx, dtype=float)
+    sel = (xs > 10) & (xs < 70)
+    popt, _ = curve_fit(lambda x, x0, w_, a: a * np.tanh(2 * (x - x0) / w_), xs[sel], phi[sel],
+                        p0=(40, Wd, 1.0))
+    assert popt[1] == pytest.approx(Wd, rel=0.03)
+    _, kappa = oracle.params_from_sigma_W(sigma, Wd)
+    d = (np.roll(phi, -1) - np.roll(phi, 1)) / 2
+    assert kappa * np.sum(d[sel] ** 2) == pytest.approx(sigma, rel=0.03)
+
+
+def test_laplace_law():
+    """Eq. 3 at rest: the hydrodynamic pressure p_h = p + phi mu (the solved p is the modified
+    pressure of the potential-form force -phi grad(mu)) jumps by sigma/R across a static
+    droplet.  Slope of dp_h against 1/R over four radii within 5 %."""
+    n, Wd, sigma = 64, 4.0, 0.01
+    Rs = [10.0, 12.0, 14.0, 16.0]
+    dps = []
+    for R in Rs:
+        w = W.static_droplet(nx=n, ny=n, R=R, W=Wd, sigma=sigma, steps=0)
+        s = oracle.Sim.from_workload(w)
+        s.step(5000)
+        acc = []
+        yy, xx = np.mgrid[0:n, 0:n]
+        r = np.hypot(xx - n / 2, yy - n / 2)
+        for _ in range(10):
+            s.step(200)
+            m = s.moments()
+            ph = m["p"] + m["phi"] * s.field(oracle.MU)
+            acc.append(ph[r < R - 2 * Wd].mean() - ph[r > R + 2 * Wd].mean())
+        dps.append(np.mean(acc))
+    slope, icpt = np.polyfit(1.0 / np.array(Rs), np.array(dps), 1)
+    assert slope == pytest.approx(sigma, rel=0.05)
+    for R, dp in zip(Rs, dps):
+        assert dp == pytest.approx(sigma / R, rel=0.05)
+
+
+def test_linear_cahn_hilliard_decay():
+    """Eq. 2 linearised about a uniform phi0 (theta''(phi0) > 0) and coupled to the pressure
+    equation Eq. 9.  A mode cos(kx) has mu' = M phi' with M = theta''(phi0) + kappa lam,
+    lam = 2 (1 - cos k) the discrete Laplacian symbol.  Force balance grad(p) = -phi0 grad(mu')
+    with d_t p = -rho cs2 div(u) (Eq. 9) gives a flow whose flux phi0 u slows the decay:
+        rate = theta_M lam M / (1 + phi0^2 M / (rho cs2)),
+    theta_M = Gamma_f (tau_f - 1/2) being the mobility of the Cahn-Hilliard equilibrium.
+    Checked within 2 % after the acoustic transient."""
+    nx, ny, phi0, eps = 32, 4, 0.8, 1e-4
+    sigma, Wd, thM, rho = 0.1, 2.0, 0.1, 1.0
+    phys = W.Physical(sigma=sigma, W=Wd, theta_M=thM, rho_A=rho, rho_B=rho)
+    k = 2 * np.pi / nx
+    xs = np.arange(nx)
+    phi = phi0 + eps * np.cos(k * xs)[None, :].repeat(ny, 0)
+    s = oracle.Sim.from_workload(W.make("ch", nx, ny, phys, 0, phi))
+    beta, kappa = oracle.params_from_sigma_W(sigma, Wd)
+    lam = 2 * (1 - np.cos(k))
+    M = 4 * beta * (3 * phi0 ** 2 - 1) + kappa * lam
+    rate = thM * lam * M / (1 + phi0 ** 2 * M / (rho * CS2))
+    amps, ts = [], []
+    s.step(1500)
+    for t in range(6):
+        m = s.moments()["phi"][0]
+        amps.append(2 * np.mean((m - m.mean()) * np.cos(k * xs)))
+        ts.append(1500 + 300 * t)
+        s.step(300)
+    fit = -np.polyfit(ts, np.log(amps), 1)[0]
+    assert fit == pytest.approx(rate, rel=0.02)
+    # without the compressible coupling the prediction would be ~20 % off: the pin sees Eq. 9
+    assert abs(fit / (thM * lam * M) - 1) > 0.1
+
+
+@pytest.mark.parametrize("phase", [+1, -1])
+def test_shear_wave_viscosity_per_phase(phase):
+    """A shear wave u_x = U sin(k y) in a single phase decays at nu k^2 with
+    nu = cs2 (tau_g - 1/2) of that phase (viscosity of Eq. 3, relaxation of Eq. 8)."""
+    nx, ny, U = 4, 64, 1e-4
+    nu_A, nu_B = 0.05, 0.12
+    phys = W.Physical(sigma=0.01, W=4.0, nu_A=nu_A, nu_B=nu_B, rho_A=1.0, rho_B=0.3)
+    k = 2 * np.pi / ny
+    ys = np.arange(ny)
+    ux = U * np.sin(k * ys)[:, None].repeat(nx, 1)
+    phi = np.full((ny, nx), float(phase))
+    s = oracle.Sim.from_workload(W.make("sw", nx, ny, phys, 0, phi, ux0=ux))
+    amps, ts = [], []
+    for t in range(6):
+        m = s.moments()["ux"][:, 0]
+        amps.append(2 * np.mean(m * np.sin(k * ys)))
+        ts.append(200 * t)
+        s.step(200)
+    fit = -np.polyfit(ts[1:], np.log(amps[1:]), 1)[0]
+    nu = nu_A if phase > 0 else nu_B
+    assert fit == pytest.approx(nu * k * k, rel=0.01)
+
+
+def test_hydrostatic_pressure_under_gravity():
+    """Eq. 3 at rest with G = -rho g y_hat between walls: dp/dy = -rho g (sign and magnitude).
+    Started from the linear hydrostatic pressure so that no acoustic transient compresses phi
+    (a compressed phi would add a slowly relaxing surface-tension force)."""
+    nx, ny, g = 4, 40, 1e-5
+    for phase, rho in ((+1, 1.0), (-1, 0.2)):
+        phys = W.Physical(sigma=0.01, W=4.0, rho_A=1.0, rho_B=0.2, gravity=g, bc_y=W.WALL)
+        y = np.arange(ny, dtype=float)[:, None].repeat(nx, 1)
+        p0 = -rho * g * (y - (ny - 1) / 2)
+        s = oracle.Sim.from_workload(W.make("h", nx, ny, phys, 0, np.full((ny, nx), float(phase)),
+                                            p0=p0))
+        s.step(6000)
+        m = s.moments()
+        slope = np.polyfit(np.arange(ny), m["p"][:, 0], 1)[0]
+        assert slope == pytest.approx(-rho * g, rel=0.005)
+        assert np.abs(m["uy"]).max() < 0.05 * g
+
+
+def test_mass_defect_matches_finite_differences():
+    """Eq. 5: d_t rho + div(rho u) = rho' div(theta_M grad mu) = s.  The oracle's s is checked
+    against an independent space-time finite-difference evaluation of
+    rho' (d_t phi + div(phi u)) on smooth periodic fields, i.e. the recovered Cahn-Hilliard
+    equation (Eq. 2, conservative form); the residual is far below |s|.  (The density form
+    d_t rho + div(rho u) itself differs from s by (rho_A + rho_B)/2 div(u), the weak
+    compressibility of Eq. 9, which on this field is larger than s.)"""
+    n = 64
+    y, x = np.mgrid[0:n, 0:n].astype(float)
+    phi = 0.75 + 0.15 * np.sin(2 * np.pi * x / n) * np.sin(2 * np.pi * y / n) + \
+        0.05 * np.cos(4 * np.pi * x / n)
+    phys = W.Physical(sigma=0.05, W=6.0, theta_M=0.1, rho_A=1.0, rho_B=0.5)
+    s = oracle.Sim.from_workload(W.make("fd", n, n, phys, 0, phi))
+    s.step(3000)    # past the acoustic transient
+    rp = (phys.rho_A - phys.rho_B) / 2
+    m_prev = s.moments()
+    s.step(1)
+    m = s.moments()
+    sdef = s.field(oracle.S)
+    s.step(1)
+    m_next = s.moments()
+
+    def ddx(a):
+        return (np.roll(a, -1, 1) - np.roll(a, 1, 1)) / 2
+
+    def ddy(a):
+        return (np.roll(a, -1, 0) - np.roll(a, 1, 0)) / 2
+
+    fd = rp * ((m_next["phi"] - m_prev["phi"]) / 2 + ddx(m["phi"] * m["ux"]) + ddy(m["phi"] * m["uy"]))
+    scale = np.abs(sdef).max()
+    assert scale > 1e-7
+    assert np.abs(fd - sdef).max() < 0.05 * scale
