@@ -1,0 +1,181 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) two-distribution D2Q9 multiphase lattice Boltzmann
+ * library.
+ *
+ * The method (Li, Luo & Gao, "Additional interfacial force in lattice Boltzmann models for
+ * incompressible multiphase flows"):
+ *   - an order-parameter distribution f_a whose zeroth moment phi tracks the interface by the
+ *     convective Cahn-Hilliard equation (Eq. 2) with chemical potential
+ *     mu = theta'(phi) - kappa lap(phi), theta = beta (phi^2 - phi*^2)^2 (Eq. 1);
+ *   - a pressure distribution gbar_a (g_a = cs2 f_a + psi w_a, psi = p - rho cs2) that solves
+ *     the pressure and velocity by Eq. 8 with forcing (e_a - u).K, K = (F_s + G) omega_a(u)
+ *     - (omega_a(u) - omega_a(0)) grad(psi), discretised to second order;
+ *   - density rho = rho_B + (phi + phi*)/(2 phi*) (rho_A - rho_B) (Eq. 4);
+ *   - a per-run flag that removes the additional interfacial force
+ *     F_a = -u [d_t rho + div(rho u)] (Eq. 12) by adding -F_a to the forcing.
+ * Surface tension force F_s = -phi grad(mu), gravity G = (0, -rho g); derivatives are isotropic
+ * central differences over the D2Q9 neighbours.
+ *
+ * Conventions
+ *   - Lattice units, dx = dt = 1, cs2 = 1/3.  Fields exchanged with the caller are row-major
+ *     float32 arrays of nx*ny values, index y*nx + x, x in [0,nx), y in [0,ny).
+ *   - Every call returns LBM_OK (0) or a negative LBM_ERR_* code; no exception crosses the ABI.
+ *     lbm_last_error() gives a thread-local message for the last failure.
+ *   - The library owns all device state of a simulation; the caller owns every buffer it
+ *     passes in.  Pointers to fields may be host or device memory (detected per call).
+ *   - Work is queued on the CUDA stream given at creation (NULL = legacy default stream).
+ *     lbm_step is asynchronous; lbm_moments and lbm_diagnostics synchronise that stream.
+ *   - One simulation must not be used from two host threads at once.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LBM_API __attribute__((visibility("default")))
+#else
+#define LBM_API
+#endif
+
+/* boundary types */
+#define LBM_PERIODIC 0
+#define LBM_WALL 1 /* no-slip wall half a cell outside the first/last row or column */
+
+/* population storage */
+#define LBM_FP32 0     /* 4-byte populations */
+#define LBM_FP16_DEV 1 /* 2-byte fp16 deviations from the lattice-weight baseline, FP32 math */
+#define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math */
+
+/* return codes */
+#define LBM_OK 0
+#define LBM_ERR_INVALID_ARG (-1)
+#define LBM_ERR_OOM (-2)
+#define LBM_ERR_BUDGET (-3)
+#define LBM_ERR_DIVERGED (-4)
+#define LBM_ERR_TIMEOUT (-5)
+#define LBM_ERR_CUDA (-6)
+
+/* Scheme parameters (lattice units).
+ *   beta, kappa   free-energy coefficients of Eq. 1 (> 0); see lbm_params_from_sigma_W.
+ *   phi_star      equilibrium order parameter (> 0); phase A (heavy) is +phi*, B is -phi*.
+ *   theta_M       Cahn-Hilliard mobility of Eq. 2 (>= 0).
+ *   tau_f         relaxation time of f (> 1/2).
+ *   tau_g_A/B     relaxation time of gbar in pure phase A / B (> 1/2); in the interface the
+ *                 dynamic viscosity rho cs2 (tau - 1/2) is interpolated linearly in the liquid
+ *                 fraction c = (phi + phi*)/(2 phi*) clamped to [0, 1].
+ *   rho_A, rho_B  phase densities (> 0), Eq. 4.
+ *   gravity       magnitude g of the body force G = (0, -rho g).
+ *   bc_x, bc_y    LBM_PERIODIC or LBM_WALL.
+ *   remove_Fa     0: scheme as first stated (Eq. 8 with F_s + G);
+ *                 1: additional interfacial force removed (forcing F_s + G + u s with
+ *                    s = rho' theta_M lap(mu) = d_t rho + div(rho u) by Eq. 5).
+ *   storage       LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV. */
+typedef struct {
+    double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
+    int bc_x, bc_y, remove_Fa, storage;
+} lbm_params;
+
+/* FP64 diagnostics of the current state (reductions in a fixed order: bitwise reproducible).
+ *   sum_phi         sum of phi over the grid (conserved, Eq. 5 integrated)
+ *   liquid_area     sum of c = clamp((phi + phi*)/(2 phi*), 0, 1)
+ *   centroid_x/y    sum(c x)/sum(c), sum(c y)/sum(c)
+ *   vel_x/y         sum(c u)/sum(c)
+ *   spread_radius   half of the largest row sum of c (half the widest liquid chord)
+ *   max_u           max |u|
+ *   p_liquid/p_gas  mean pressure over phi > 0.9 phi* / phi < -0.9 phi*
+ *   finite          0 if sum_phi or max_u is not finite (the run has diverged) */
+typedef struct {
+    long long step;
+    double sum_phi, liquid_area, centroid_x, centroid_y, vel_x, vel_y;
+    double spread_radius, max_u, p_liquid, p_gas;
+    int finite, pad;
+} lbm_diag;
+
+typedef struct lbm_sim lbm_sim;
+
+/* kappa = 3 sigma W / (8 phi*^2), beta = 3 sigma / (4 W phi*^4): the planar equilibrium of
+ * Eq. 1 is phi* tanh(2x/W) with surface tension sigma.  Returns LBM_ERR_INVALID_ARG unless
+ * sigma, W, phi_star > 0. */
+LBM_API int lbm_params_from_sigma_W(double sigma, double W, double phi_star, double* beta, double* kappa);
+
+/* BGK relaxation time of a kinematic viscosity: tau = nu / cs2 + 1/2. */
+LBM_API double lbm_tau_from_nu(double nu);
+
+/* Device bytes one simulation of nx x ny holds (both population buffers, field scratch and
+ * reduction scratch) for the given storage. */
+LBM_API size_t lbm_device_bytes(int nx, int ny, int storage);
+
+/* Create a simulation on the current CUDA device.  nx, ny >= 3 (>= 4 along a walled axis);
+ * parameters are validated (tau > 1/2, densities, beta, kappa, phi* > 0, theta_M >= 0).
+ * cuda_stream: a cudaStream_t (may be NULL).  On success *out owns cudaMalloc'd state.
+ * Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM (device allocation failed), LBM_ERR_CUDA. */
+LBM_API int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out);
+
+/* Set the state at t = 0 from phi0, ux0, uy0, p0 (nx*ny float32 each, host or device; ux0,
+ * uy0 and p0 may be NULL for zero): f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0).
+ * Asynchronous for device inputs; host inputs are copied before return. */
+LBM_API int lbm_init_fields(lbm_sim* sim, const float* phi0, const float* ux0, const float* uy0,
+                    const float* p0);
+
+/* Advance n >= 0 time steps (asynchronous, queued on the simulation's stream). */
+LBM_API int lbm_step(lbm_sim* sim, int n);
+
+/* Macroscopic fields of the current state (phi, rho, ux, uy, p; any pointer may be NULL),
+ * row-major nx*ny float32 each, host or device.  Synchronises the stream. */
+LBM_API int lbm_moments(lbm_sim* sim, float* phi, float* rho, float* ux, float* uy, float* p);
+
+/* FP64 diagnostics of the current state into *out (host).  Returns LBM_ERR_DIVERGED (and
+ * fills *out, finite = 0) when the state is no longer finite.  Synchronises the stream. */
+LBM_API int lbm_diagnostics(lbm_sim* sim, lbm_diag* out);
+
+/* Free the simulation's device state (synchronises its stream first). */
+LBM_API int lbm_destroy(lbm_sim* sim);
+
+/* Number of time steps taken since lbm_init_fields. */
+LBM_API long long lbm_step_count(const lbm_sim* sim);
+
+/* Replace the stream the simulation queues its work on (cudaStream_t, may be NULL). */
+LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
+
+/* Tile shape of the fused step kernel: threads per CTA (64, 128 or 256; the CTA covers
+ * threads - 6 interior columns) and rows per CTA (>= 1).  0 keeps the current value. */
+LBM_API int lbm_set_tile(lbm_sim* sim, int threads, int seg_rows);
+
+/* Kernel launches issued by this simulation since creation (step, init, moments,
+ * reductions). */
+LBM_API long long lbm_launch_count(const lbm_sim* sim);
+
+/* Static description of an error code. */
+LBM_API const char* lbm_strerror(int code);
+
+/* Message of the last failed call on this host thread ("" if none). */
+LBM_API const char* lbm_last_error(void);
+
+/* ------------------------------------------------------------------ ragged batches
+ * A batch advances many independent simulations (different sizes and parameters) with one
+ * launch per time step over a work list of tiles from all of them.  Simulations stay owned by
+ * the caller; the batch references them.  budget_bytes caps the summed lbm_device_bytes of
+ * its members (0 = no cap).  lbm_batch_step(k) advances every member by k steps (one CUDA
+ * graph replay for a fixed membership); members keep stepping on the batch's stream. */
+typedef struct lbm_batch lbm_batch;
+
+LBM_API int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch** out);
+/* Add a simulation (it must not be in another batch).  LBM_ERR_BUDGET if it does not fit. */
+LBM_API int lbm_batch_add(lbm_batch* b, lbm_sim* sim, int* slot);
+LBM_API int lbm_batch_remove(lbm_batch* b, int slot);
+LBM_API int lbm_batch_step(lbm_batch* b, int k);
+/* Members, device bytes in use. */
+LBM_API int lbm_batch_size(const lbm_batch* b);
+LBM_API size_t lbm_batch_bytes(const lbm_batch* b);
+LBM_API int lbm_batch_destroy(lbm_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,183 @@
+"""GB300-native two-distribution D2Q9 multiphase lattice Boltzmann library (Python side).
+
+Thin layer over the C ABI in ``include/lbm.h``: every step of the method runs in the CUDA
+kernels of ``liblbm.so``; this module only marshals arguments.  PyTorch is used for device
+buffers and streams when the caller passes tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (LBM_BF16_DEV, LBM_ERR_BUDGET, LBM_ERR_DIVERGED, LBM_FP16_DEV, LBM_FP32,
+                   LBM_PERIODIC, LBM_WALL, LBMError, lbm_diag, lbm_params)
+
+__all__ = ["Sim", "Batch", "LBMError", "params_from_physical", "lbm_params", "LBM_FP32",
+           "LBM_FP16_DEV", "LBM_BF16_DEV", "LBM_PERIODIC", "LBM_WALL", "LBM_ERR_DIVERGED",
+           "LBM_ERR_BUDGET", "device_bytes"]
+
+
+def lib():
+    return _lib.load()
+
+
+def _ptr(a):
+    """Address of a host numpy array or a device torch tensor (float32, contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float32 and a.flags.c_contiguous, "float32 C-contiguous array required"
+        return a.ctypes.data
+    # torch tensor
+    assert a.dtype.__repr__().endswith("float32") and a.is_contiguous(), "float32 contiguous tensor required"
+    return a.data_ptr()
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream   # torch.cuda.Stream
+
+
+def params_from_physical(phys, storage=LBM_FP32) -> lbm_params:
+    """Scheme parameters of a ``workloads.Physical`` record, converted by the library."""
+    b, k = ctypes.c_double(), ctypes.c_double()
+    _lib.check(lib().lbm_params_from_sigma_W(phys.sigma, phys.W, phys.phi_star, ctypes.byref(b),
+                                             ctypes.byref(k)))
+    return lbm_params(beta=b.value, kappa=k.value, phi_star=phys.phi_star, theta_M=phys.theta_M,
+                      tau_f=phys.tau_f, tau_g_A=lib().lbm_tau_from_nu(phys.nu_A),
+                      tau_g_B=lib().lbm_tau_from_nu(phys.nu_B), rho_A=phys.rho_A,
+                      rho_B=phys.rho_B, gravity=phys.gravity, bc_x=phys.bc_x, bc_y=phys.bc_y,
+                      remove_Fa=phys.remove_Fa, storage=storage)
+
+
+def device_bytes(nx, ny, storage=LBM_FP32) -> int:
+    return int(lib().lbm_device_bytes(nx, ny, storage))
+
+
+class Sim:
+    """One simulation with device-resident state (owned by the library)."""
+
+    def __init__(self, nx, ny, params: lbm_params, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.params = params
+        h = ctypes.c_void_p()
+        _lib.check(lib().lbm_create(self.nx, self.ny, ctypes.byref(params), _stream_handle(stream),
+                                    ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, storage=LBM_FP32, stream=None, init=True, tile=None):
+        s = cls(w.nx, w.ny, params_from_physical(w.phys, storage), stream=stream)
+        if tile is not None:
+            s.set_tile(*tile)
+        if init:
+            s.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
+        return s
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lbm_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tile(self, threads=0, seg_rows=0):
+        _lib.check(lib().lbm_set_tile(self._h, int(threads), int(seg_rows)))
+
+    def set_stream(self, stream):
+        _lib.check(lib().lbm_set_stream(self._h, _stream_handle(stream)))
+
+    def init_fields(self, phi0, ux0=None, uy0=None, p0=None):
+        _lib.check(lib().lbm_init_fields(self._h, _ptr(phi0), _ptr(ux0), _ptr(uy0), _ptr(p0)))
+
+    def step(self, n=1):
+        _lib.check(lib().lbm_step(self._h, int(n)))
+
+    @property
+    def step_count(self):
+        return int(lib().lbm_step_count(self._h))
+
+    @property
+    def launch_count(self):
+        return int(lib().lbm_launch_count(self._h))
+
+    def moments(self, out=None):
+        """phi, rho, ux, uy, p as (ny, nx) float32 host arrays (or into the given dict of
+        host arrays / device tensors)."""
+        names = ("phi", "rho", "ux", "uy", "p")
+        if out is None:
+            out = {k: np.empty((self.ny, self.nx), np.float32) for k in names}
+        _lib.check(lib().lbm_moments(self._h, *[_ptr(out.get(k)) for k in names]))
+        return out
+
+    def diagnostics(self, raise_on_divergence=False):
+        d = lbm_diag()
+        rc = lib().lbm_diagnostics(self._h, ctypes.byref(d))
+        if rc != 0 and (rc != LBM_ERR_DIVERGED or raise_on_divergence):
+            _lib.check(rc)
+        return d.as_dict()
+
+
+class Batch:
+    """Ragged batch: member simulations advance together, one persistent launch per step."""
+
+    def __init__(self, budget_bytes=0, stream=None):
+        h = ctypes.c_void_p()
+        _lib.check(lib().lbm_batch_create(int(budget_bytes), _stream_handle(stream), ctypes.byref(h)))
+        self._h = h
+        self.members = {}
+
+    def add(self, sim: Sim) -> int:
+        slot = ctypes.c_int()
+        _lib.check(lib().lbm_batch_add(self._h, sim.handle, ctypes.byref(slot)))
+        self.members[slot.value] = sim
+        return slot.value
+
+    def try_add(self, sim: Sim):
+        """Slot, or None when the budget is exhausted."""
+        slot = ctypes.c_int()
+        rc = lib().lbm_batch_add(self._h, sim.handle, ctypes.byref(slot))
+        if rc == LBM_ERR_BUDGET:
+            return None
+        _lib.check(rc)
+        self.members[slot.value] = sim
+        return slot.value
+
+    def remove(self, slot: int):
+        _lib.check(lib().lbm_batch_remove(self._h, int(slot)))
+        return self.members.pop(slot)
+
+    def step(self, k=1):
+        _lib.check(lib().lbm_batch_step(self._h, int(k)))
+
+    @property
+    def size(self):
+        return int(lib().lbm_batch_size(self._h))
+
+    @property
+    def bytes(self):
+        return int(lib().lbm_batch_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().lbm_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,320 @@
+// Host runtime and C ABI of liblbm: simulation objects, parameter checks, field transfer,
+// step launches and diagnostics.  See include/lbm.h for the contract of every entry point.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA;
+}
+
+Phys make_phys(const lbm_params& p) {
+  Phys P{};
+  const double cs2 = 1.0 / 3.0;
+  P.four_beta = (float)(4.0 * p.beta);
+  P.kappa = (float)p.kappa;
+  P.phi_star = (float)p.phi_star;
+  P.phi_star2 = (float)(p.phi_star * p.phi_star);
+  P.inv_2phistar = (float)(1.0 / (2.0 * p.phi_star));
+  P.rho_B = (float)p.rho_B;
+  P.drho = (float)(p.rho_A - p.rho_B);
+  P.rho_prime = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star));
+  P.s_coef = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) * p.theta_M);
+  P.gravity = (float)p.gravity;
+  P.omega_f = (float)(1.0 / p.tau_f);
+  P.three_gamma_f = (float)(3.0 * p.theta_M / (p.tau_f - 0.5));
+  P.mu_A = (float)(p.rho_A * cs2 * (p.tau_g_A - 0.5));
+  P.mu_B = (float)(p.rho_B * cs2 * (p.tau_g_B - 0.5));
+  P.remove_Fa = p.remove_Fa ? 1 : 0;
+  return P;
+}
+
+void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, int* n_strips, int* seg_out) {
+  const int wmax = nt - 6;
+  const int ns = (nx + wmax - 1) / wmax;
+  *n_strips = ns;
+  *tile_w = (nx + ns - 1) / ns;
+  if (seg_h <= 0) {
+    const int segs = slots > ns ? (slots + ns - 1) / ns : 1;
+    seg_h = (ny + segs - 1) / segs;
+    if (seg_h < 8) seg_h = 8;
+  }
+  *seg_out = seg_h;
+}
+
+Grid make_grid(const lbm_sim* s, const float* src, float* dst) {
+  Grid g{};
+  g.src = src;
+  g.dst = dst;
+  g.plane = (int)s->plane;
+  g.nx = s->nx;
+  g.ny = s->ny;
+  g.pitch = s->pitch;
+  g.bc_x = s->params.bc_x;
+  g.bc_y = s->params.bc_y;
+  tile_geometry(s->nx, s->ny, s->nt, s->seg_h, s->sms * (s->occ > 0 ? s->occ : 1), &g.tile_w, &g.n_strips, &g.seg_h);
+  return g;
+}
+
+static int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int check_params(int nx, int ny, const lbm_params* p) {
+  if (!p) return set_error("params is NULL"), LBM_ERR_INVALID_ARG;
+  if ((p->bc_x != LBM_PERIODIC && p->bc_x != LBM_WALL) || (p->bc_y != LBM_PERIODIC && p->bc_y != LBM_WALL))
+    return set_error("bc_x/bc_y must be LBM_PERIODIC or LBM_WALL"), LBM_ERR_INVALID_ARG;
+  if (nx < (p->bc_x == LBM_WALL ? 4 : 3) || ny < (p->bc_y == LBM_WALL ? 4 : 3))
+    return set_error("grid %dx%d too small (>= 3, >= 4 along a walled axis)", nx, ny), LBM_ERR_INVALID_ARG;
+  if ((long long)ny * pitch_of(nx) >= (1LL << 31) / N_PLANES)
+    return set_error("grid %dx%d too large", nx, ny), LBM_ERR_INVALID_ARG;
+  if (!(p->tau_f > 0.5 && p->tau_g_A > 0.5 && p->tau_g_B > 0.5))
+    return set_error("relaxation times must exceed 1/2"), LBM_ERR_INVALID_ARG;
+  if (!(p->rho_A > 0 && p->rho_B > 0)) return set_error("densities must be positive"), LBM_ERR_INVALID_ARG;
+  if (!(p->beta > 0 && p->kappa > 0 && p->phi_star > 0))
+    return set_error("beta, kappa and phi_star must be positive"), LBM_ERR_INVALID_ARG;
+  if (!(p->theta_M >= 0) || !(p->gravity == p->gravity))
+    return set_error("theta_M must be >= 0 and gravity finite"), LBM_ERR_INVALID_ARG;
+  if (p->storage != LBM_FP32)
+    return set_error("storage %d not available in this build", p->storage), LBM_ERR_INVALID_ARG;
+  return LBM_OK;
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+extern "C" {
+
+int lbm_params_from_sigma_W(double sigma, double W, double phi_star, double* beta, double* kappa) {
+  if (!(sigma > 0 && W > 0 && phi_star > 0) || !beta || !kappa) {
+    set_error("sigma, W and phi_star must be positive");
+    return LBM_ERR_INVALID_ARG;
+  }
+  *kappa = 3.0 * sigma * W / (8.0 * phi_star * phi_star);
+  *beta = 3.0 * sigma / (4.0 * W * phi_star * phi_star * phi_star * phi_star);
+  return LBM_OK;
+}
+
+double lbm_tau_from_nu(double nu) { return 3.0 * nu + 0.5; }
+
+size_t lbm_device_bytes(int nx, int ny, int storage) {
+  (void)storage;
+  const size_t plane = (size_t)ny * pitch_of(nx);
+  return 2 * N_PLANES * plane * sizeof(float) + N_FIELDS * plane * sizeof(float) +
+         ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double);
+}
+
+int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out) {
+  if (!out) return set_error("out is NULL"), LBM_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_params(nx, ny, params);
+  if (rc) return rc;
+  lbm_sim* s = new (std::nothrow) lbm_sim();
+  if (!s) return set_error("host allocation failed"), LBM_ERR_OOM;
+  s->nx = nx;
+  s->ny = ny;
+  s->pitch = pitch_of(nx);
+  s->plane = (long long)ny * s->pitch;
+  s->params = *params;
+  s->phys = make_phys(*params);
+  s->stream = (cudaStream_t)cuda_stream;
+  const size_t pop_bytes = (size_t)N_PLANES * s->plane * sizeof(float);
+  cudaError_t e;
+  int dev = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) {
+    rc = cuda_fail(e, "lbm_create device query");
+    delete s;
+    return rc;
+  }
+  s->occ = tile_occupancy(s->nt);
+  if ((e = cudaMalloc(&s->buf[0], pop_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&s->buf[1], pop_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&s->fields, (size_t)N_FIELDS * s->plane * sizeof(float))) != cudaSuccess ||
+      (e = cudaMalloc(&s->red, ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->h_diag, sizeof(lbm_diag))) != cudaSuccess) {
+    rc = cuda_fail(e, "lbm_create allocation");
+    lbm_destroy(s);
+    return rc;
+  }
+  // zero the pad columns once so no uninitialised memory is ever read back
+  cudaMemsetAsync(s->buf[0], 0, pop_bytes, s->stream);
+  cudaMemsetAsync(s->buf[1], 0, pop_bytes, s->stream);
+  cudaMemsetAsync(s->fields, 0, (size_t)N_FIELDS * s->plane * sizeof(float), s->stream);
+  if ((e = cudaGetLastError()) != cudaSuccess) {
+    rc = cuda_fail(e, "lbm_create memset");
+    lbm_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return LBM_OK;
+}
+
+static int upload_field(lbm_sim* s, int k, const float* src) {
+  float* dst = s->fields + (long long)k * s->plane;
+  cudaError_t e;
+  if (!src) {
+    e = cudaMemsetAsync(dst, 0, (size_t)s->plane * sizeof(float), s->stream);
+  } else {
+    const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = cudaMemcpy2DAsync(dst, (size_t)s->pitch * sizeof(float), src, (size_t)s->nx * sizeof(float),
+                          (size_t)s->nx * sizeof(float), s->ny, kind, s->stream);
+  }
+  return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_init_fields upload");
+}
+
+int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float* uy0, const float* p0) {
+  if (!s || !phi0) return set_error("sim and phi0 are required"), LBM_ERR_INVALID_ARG;
+  int rc;
+  if ((rc = upload_field(s, 0, phi0)) || (rc = upload_field(s, 2, ux0)) || (rc = upload_field(s, 3, uy0)) ||
+      (rc = upload_field(s, 4, p0)))
+    return rc;
+  cudaError_t e = launch_init(s, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields launch");
+  s->launches += 2;
+  s->steps = 0;
+  // host inputs must be consumed before return (pageable copies already are; pinned ones not)
+  if (!is_device_ptr(phi0) && (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+    return cuda_fail(e, "lbm_init_fields sync");
+  return LBM_OK;
+}
+
+int lbm_step(lbm_sim* s, int n) {
+  if (!s || n < 0) return set_error("invalid sim or step count"), LBM_ERR_INVALID_ARG;
+  if (s->batch) return set_error("simulation is a batch member; step it through its batch"), LBM_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) {
+    Grid g = make_grid(s, s->buf[s->cur], s->buf[s->cur ^ 1]);
+    cudaError_t e = launch_step(s->phys, g, s->nt, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_step launch");
+    s->cur ^= 1;
+    s->steps++;
+    s->launches++;
+  }
+  return LBM_OK;
+}
+
+static int compute_moments(lbm_sim* s) {
+  Grid g = make_grid(s, s->buf[s->cur], nullptr);
+  MomentOut mo{s->fields, s->fields + s->plane, s->fields + 2 * s->plane, s->fields + 3 * s->plane,
+               s->fields + 4 * s->plane};
+  cudaError_t e = launch_moments(s->phys, g, mo, s->nt, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "moments launch");
+  s->launches++;
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float* p) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  int rc = compute_moments(s);
+  if (rc) return rc;
+  float* outs[5] = {phi, rho, ux, uy, p};
+  for (int k = 0; k < 5; ++k) {
+    if (!outs[k]) continue;
+    const cudaMemcpyKind kind = is_device_ptr(outs[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaError_t e = cudaMemcpy2DAsync(outs[k], (size_t)s->nx * sizeof(float), s->fields + (long long)k * s->plane,
+                                      (size_t)s->pitch * sizeof(float), (size_t)s->nx * sizeof(float), s->ny, kind,
+                                      s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_moments copy");
+  }
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_moments sync");
+}
+
+int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {
+  if (!s || !out) return set_error("sim and out are required"), LBM_ERR_INVALID_ARG;
+  int rc = compute_moments(s);
+  if (rc) return rc;
+  cudaError_t e = launch_diag(s, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
+  s->launches += 2;
+  e = cudaMemcpyAsync(s->h_diag, s->red + (long long)s->ny * DIAG_PARTIALS, sizeof(lbm_diag),
+                      cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
+  *out = *s->h_diag;
+  if (!out->finite) {
+    set_error("simulation diverged (non-finite state) at step %lld", out->step);
+    return LBM_ERR_DIVERGED;
+  }
+  return LBM_OK;
+}
+
+int lbm_destroy(lbm_sim* s) {
+  if (!s) return LBM_OK;
+  if (s->stream || s->buf[0]) cudaStreamSynchronize(s->stream);
+  cudaFree(s->buf[0]);
+  cudaFree(s->buf[1]);
+  cudaFree(s->fields);
+  cudaFree(s->red);
+  if (s->h_diag) cudaFreeHost(s->h_diag);
+  delete s;
+  return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_sim* s) { return s ? s->steps : -1; }
+
+int lbm_set_stream(lbm_sim* s, void* stream) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  s->stream = (cudaStream_t)stream;
+  return LBM_OK;
+}
+
+int lbm_set_tile(lbm_sim* s, int threads, int seg_rows) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  if (threads && threads != 64 && threads != 128 && threads != 256)
+    return set_error("threads must be 64, 128 or 256"), LBM_ERR_INVALID_ARG;
+  if (seg_rows < 0) return set_error("seg_rows must be >= 1"), LBM_ERR_INVALID_ARG;
+  if (threads) {
+    s->nt = threads;
+    s->occ = tile_occupancy(threads);
+  }
+  if (seg_rows) s->seg_h = seg_rows;
+  return LBM_OK;
+}
+
+long long lbm_launch_count(const lbm_sim* s) { return s ? s->launches : -1; }
+
+const char* lbm_strerror(int code) {
+  switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_ERR_INVALID_ARG: return "invalid argument";
+    case LBM_ERR_OOM: return "out of device memory";
+    case LBM_ERR_BUDGET: return "device-memory budget exceeded";
+    case LBM_ERR_DIVERGED: return "simulation diverged";
+    case LBM_ERR_TIMEOUT: return "timed out";
+    case LBM_ERR_CUDA: return "CUDA error";
+    default: return "unknown error";
+  }
+}
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

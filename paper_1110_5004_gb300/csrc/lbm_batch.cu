@@ -1,0 +1,275 @@
+// Ragged batches: many independent simulations (any sizes and parameters) advanced by one
+// persistent launch per time step over a work list of (simulation, strip, segment) tiles.
+// k steps are captured once as a CUDA graph of k launches and replayed while the membership is
+// unchanged.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel,
+// so a member's state is bitwise the same alone or inside any mix.
+#include <algorithm>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+struct SimDesc {
+  Phys P;
+  Grid g;                 // src/dst unused; buffers below
+  const float* buf0;
+  float* buf1;
+  int cur0;               // buffer holding the state when the graph replay starts
+  int pad;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
+                                              int n_work, int parity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
+  for (int w = blockIdx.x; w < n_work; w += gridDim.x) {
+    const int4 it = work[w];
+    const SimDesc& d = sims[it.x];
+    Grid g = d.g;
+    const bool odd = ((d.cur0 + parity) & 1) != 0;
+    g.src = odd ? d.buf1 : d.buf0;
+    g.dst = odd ? const_cast<float*>(d.buf0) : d.buf1;
+    run_tile<NT, MODE_STEP>(d.P, g, MomentOut{}, it.y, it.z, sm);
+    __syncthreads();  // shared rings are reused by the next tile
+  }
+}
+
+}  // namespace lbm
+
+using namespace lbm;
+
+static cudaError_t set_batch_attr(int nt) {
+  switch (nt) {
+    case 64: return cudaFuncSetAttribute(k_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<64>));
+    case 256: return cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
+    default: return cudaFuncSetAttribute(k_batch<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<128>));
+  }
+}
+
+struct lbm_batch {
+  size_t budget = 0;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;          // private stream for graph capture
+  std::vector<lbm_sim*> slots;         // nullptr = free slot
+  int nt = 128;
+  int seg_h = 32;                      // rows per tile for members without their own choice
+  bool dirty = true;                   // descriptors / work list need rebuilding
+  SimDesc* d_sims = nullptr;
+  int4* d_work = nullptr;
+  size_t cap_sims = 0, cap_work = 0;
+  int n_work = 0;
+  int grid = 0;
+  int flip = 0;                        // parity offset of every member since the last rebuild
+  std::map<int, cudaGraphExec_t> graphs;  // 2k + flip -> executable graph for the membership
+};
+
+static void drop_graphs(lbm_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+static int rebuild(lbm_batch* b) {
+  std::vector<SimDesc> sims;
+  std::vector<int4> work;
+  std::vector<int> members;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (b->slots[i]) members.push_back((int)i);
+  // interleave the members' tiles so concurrent CTAs spread over simulations
+  std::vector<std::vector<int4>> per;
+  for (size_t m = 0; m < members.size(); ++m) {
+    lbm_sim* s = b->slots[members[m]];
+    SimDesc d{};
+    d.P = s->phys;
+    Grid g = make_grid(s, nullptr, nullptr);
+    // one wave of the batch kernel is shared by all members: size segments for the batch
+    tile_geometry(s->nx, s->ny, b->nt, s->seg_h ? s->seg_h : b->seg_h, 0, &g.tile_w, &g.n_strips, &g.seg_h);
+    d.g = g;
+    d.buf0 = s->buf[0];
+    d.buf1 = s->buf[1];
+    d.cur0 = s->cur;
+    sims.push_back(d);
+    std::vector<int4> tl;
+    const int nseg = (s->ny + g.seg_h - 1) / g.seg_h;
+    for (int sg = 0; sg < nseg; ++sg)
+      for (int st = 0; st < g.n_strips; ++st) tl.push_back(make_int4((int)m, st, sg, 0));
+    per.push_back(std::move(tl));
+  }
+  size_t most = 0;
+  for (auto& v : per) most = std::max(most, v.size());
+  for (size_t k = 0; k < most; ++k)
+    for (auto& v : per)
+      if (k < v.size()) work.push_back(v[k]);
+  cudaError_t e;
+  if (sims.size() > b->cap_sims) {
+    cudaFree(b->d_sims);
+    b->d_sims = nullptr;
+    b->cap_sims = 0;
+    if ((e = cudaMalloc(&b->d_sims, sims.size() * sizeof(SimDesc))) != cudaSuccess) return cuda_fail(e, "batch descriptors");
+    b->cap_sims = sims.size();
+  }
+  if (work.size() > b->cap_work) {
+    cudaFree(b->d_work);
+    b->d_work = nullptr;
+    b->cap_work = 0;
+    if ((e = cudaMalloc(&b->d_work, work.size() * sizeof(int4))) != cudaSuccess) return cuda_fail(e, "batch work list");
+    b->cap_work = work.size();
+  }
+  if (!sims.empty() &&
+      (e = cudaMemcpyAsync(b->d_sims, sims.data(), sims.size() * sizeof(SimDesc), cudaMemcpyHostToDevice, b->stream)) !=
+          cudaSuccess)
+    return cuda_fail(e, "batch descriptor upload");
+  if (!work.empty() &&
+      (e = cudaMemcpyAsync(b->d_work, work.data(), work.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream)) !=
+          cudaSuccess)
+    return cuda_fail(e, "batch work upload");
+  // host vectors die here: make the uploads complete first
+  if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_fail(e, "batch upload sync");
+  b->n_work = (int)work.size();
+  int dev = 0, sms = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if ((e = set_batch_attr(b->nt)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+  switch (b->nt) {
+    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<64>, 64, sizeof(Smem<64>)); break;
+    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<256>, 256, sizeof(Smem<256>)); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<128>, 128, sizeof(Smem<128>)); break;
+  }
+  b->grid = std::max(1, std::min(b->n_work, sms * std::max(occ, 1)));
+  b->flip = 0;
+  drop_graphs(b);
+  b->dirty = false;
+  return LBM_OK;
+}
+
+static cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t st) {
+  switch (b->nt) {
+    case 64: k_batch<64><<<b->grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    case 256: k_batch<256><<<b->grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    default: k_batch<128><<<b->grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+  }
+  return cudaGetLastError();
+}
+
+extern "C" {
+
+int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch** out) {
+  if (!out) return set_error("out is NULL"), LBM_ERR_INVALID_ARG;
+  lbm_batch* b = new (std::nothrow) lbm_batch();
+  if (!b) return set_error("host allocation failed"), LBM_ERR_OOM;
+  b->budget = budget_bytes;
+  b->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    delete b;
+    return cuda_fail(e, "batch stream");
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+int lbm_batch_add(lbm_batch* b, lbm_sim* s, int* slot) {
+  if (!b || !s) return set_error("batch and sim are required"), LBM_ERR_INVALID_ARG;
+  if (s->batch) return set_error("simulation already belongs to a batch"), LBM_ERR_INVALID_ARG;
+  const size_t need = lbm_device_bytes(s->nx, s->ny, s->params.storage);
+  if (b->budget && b->bytes + need > b->budget) {
+    set_error("batch budget: %zu + %zu > %zu bytes", b->bytes, need, b->budget);
+    return LBM_ERR_BUDGET;
+  }
+  // the member's earlier work (init, steps) was queued on its own stream
+  cudaStreamSynchronize(s->stream);
+  int k = -1;
+  for (size_t i = 0; i < b->slots.size(); ++i)
+    if (!b->slots[i]) {
+      k = (int)i;
+      break;
+    }
+  if (k < 0) {
+    k = (int)b->slots.size();
+    b->slots.push_back(nullptr);
+  }
+  b->slots[k] = s;
+  s->batch = b;
+  b->bytes += need;
+  b->dirty = true;
+  if (slot) *slot = k;
+  return LBM_OK;
+}
+
+int lbm_batch_remove(lbm_batch* b, int slot) {
+  if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
+    return set_error("invalid batch slot %d", slot), LBM_ERR_INVALID_ARG;
+  lbm_sim* s = b->slots[slot];
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch remove sync");
+  s->batch = nullptr;
+  b->bytes -= lbm_device_bytes(s->nx, s->ny, s->params.storage);
+  b->slots[slot] = nullptr;
+  b->dirty = true;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch* b, int k) {
+  if (!b || k < 0) return set_error("invalid batch or step count"), LBM_ERR_INVALID_ARG;
+  if (k == 0) return LBM_OK;
+  int rc;
+  if (b->dirty && (rc = rebuild(b))) return rc;
+  if (b->n_work == 0) return LBM_OK;
+  cudaGraphExec_t exec = nullptr;
+  const int key = 2 * k + b->flip;
+  auto it = b->graphs.find(key);
+  if (it != b->graphs.end()) {
+    exec = it->second;
+  } else {
+    cudaGraph_t graph;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
+    for (int i = 0; i < k && e == cudaSuccess; ++i) e = launch_batch(b, b->flip + i, b->cap);
+    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch capture launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture end");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+    b->graphs[key] = exec;
+  }
+  cudaError_t e = cudaGraphLaunch(exec, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  bool flip = (k & 1) != 0;
+  for (lbm_sim* s : b->slots) {
+    if (!s) continue;
+    s->steps += k;
+    s->launches += k;
+    if (flip) s->cur ^= 1;
+  }
+  if (flip) b->flip ^= 1;
+  return LBM_OK;
+}
+
+int lbm_batch_size(const lbm_batch* b) {
+  if (!b) return 0;
+  int n = 0;
+  for (lbm_sim* s : b->slots) n += s != nullptr;
+  return n;
+}
+
+size_t lbm_batch_bytes(const lbm_batch* b) { return b ? b->bytes : 0; }
+
+int lbm_batch_destroy(lbm_batch* b) {
+  if (!b) return LBM_OK;
+  cudaStreamSynchronize(b->stream);
+  for (lbm_sim* s : b->slots)
+    if (s) s->batch = nullptr;
+  drop_graphs(b);
+  cudaFree(b->d_sims);
+  cudaFree(b->d_work);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return LBM_OK;
+}
+
+}  // extern "C"

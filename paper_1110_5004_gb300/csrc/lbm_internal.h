@@ -1,0 +1,51 @@
+// Host-side internals shared by the translation units of liblbm (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <string>
+
+#include "../../include/lbm.h"
+#include "lbm_device.cuh"
+
+struct lbm_sim {
+  int nx = 0, ny = 0, pitch = 0;
+  long long plane = 0;      // elements per plane
+  lbm_params params{};
+  lbm::Phys phys{};
+  cudaStream_t stream = nullptr;
+  float* buf[2] = {nullptr, nullptr};  // N_PLANES planes each (post-collision state)
+  int cur = 0;                         // buffer holding the current state
+  float* fields = nullptr;             // 6 planes: phi, rho, ux, uy, p, mu (moments and init)
+  double* red = nullptr;               // reduction scratch: ny rows x 12 partials + final record
+  lbm_diag* h_diag = nullptr;          // pinned host copy of the final record
+  long long steps = 0;
+  long long launches = 0;
+  int nt = 128;                        // threads per CTA of the step kernel
+  int seg_h = 0;                       // rows per CTA (0: chosen to fill the GPU)
+  int sms = 0;                         // multiprocessors of the device
+  int occ = 0;                         // resident step CTAs per SM at the current nt
+  lbm_batch* batch = nullptr;
+};
+
+namespace lbm {
+
+constexpr int N_FIELDS = 6;
+constexpr int DIAG_PARTIALS = 12;
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+Phys make_phys(const lbm_params& p);
+Grid make_grid(const lbm_sim* s, const float* src, float* dst);
+// Strip width, strip count and segment height for an nx x ny grid: strips of at most nt - 6
+// columns with balanced widths; seg_h = 0 picks the height that puts about one full wave of
+// CTAs (slots = SMs x CTAs per SM) on the device.
+void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, int* n_strips, int* seg_out);
+int tile_occupancy(int nt);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_step(const Phys& P, const Grid& g, int nt, cudaStream_t st);
+cudaError_t launch_moments(const Phys& P, const Grid& g, const MomentOut& mo, int nt, cudaStream_t st);
+cudaError_t launch_init(const lbm_sim* s, cudaStream_t st);  // from fields[phi, -, ux, uy, p]
+cudaError_t launch_diag(const lbm_sim* s, cudaStream_t st);  // from fields -> red -> final record
+
+}  // namespace lbm

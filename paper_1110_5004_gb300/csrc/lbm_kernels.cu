@@ -1,0 +1,265 @@
+// Kernels of the two-distribution D2Q9 multiphase LBM: fused step, moments, initial state and
+// FP64 diagnostics, with their launchers.
+#include <math.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// ------------------------------------------------------------------ fused step / moments
+
+template <int NT, int MODE>
+__global__ void __launch_bounds__(NT) k_tiles(Phys P, Grid g, MomentOut mo) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
+  const int strip = blockIdx.x % g.n_strips;
+  const int seg = blockIdx.x / g.n_strips;
+  run_tile<NT, MODE>(P, g, mo, strip, seg, sm);
+}
+
+static int n_tiles(const Grid& g) { return g.n_strips * ((g.ny + g.seg_h - 1) / g.seg_h); }
+
+template <int NT, int MODE>
+static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
+  static bool attr_set = false;   // one GPU per process
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(Smem<NT>));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  k_tiles<NT, MODE><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_tiles(const Phys& P, const Grid& g, const MomentOut& mo, int nt, cudaStream_t st) {
+  switch (nt) {
+    case 64: return launch_nt<64, MODE>(P, g, mo, st);
+    case 128: return launch_nt<128, MODE>(P, g, mo, st);
+    case 256: return launch_nt<256, MODE>(P, g, mo, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int NT>
+static int occupancy_nt() {
+  int occ = 0;
+  // the dynamic shared-memory size above 48 KB is only admitted once the attribute is set
+  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<NT>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP>, NT, sizeof(Smem<NT>));
+  cudaGetLastError();
+  return occ > 0 ? occ : 1;
+}
+
+int tile_occupancy(int nt) {
+  switch (nt) {
+    case 64: return occupancy_nt<64>();
+    case 256: return occupancy_nt<256>();
+    default: return occupancy_nt<128>();
+  }
+}
+
+cudaError_t launch_step(const Phys& P, const Grid& g, int nt, cudaStream_t st) {
+  return launch_tiles<MODE_STEP>(P, g, MomentOut{}, nt, st);
+}
+
+cudaError_t launch_moments(const Phys& P, const Grid& g, const MomentOut& mo, int nt, cudaStream_t st) {
+  return launch_tiles<MODE_MOMENTS>(P, g, mo, nt, st);
+}
+
+// ------------------------------------------------------------------ initial state
+// fields: [0] phi0, [1] (unused), [2] ux0, [3] uy0, [4] p0, [5] mu0 -- pitched planes.
+
+__global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx) return;
+  const float* phi = fields;
+  float* mu = fields + 5 * (long long)g.plane;
+  auto at = [&](int dx, int dy) {
+    int xx = x + dx, yy = y + dy;
+    xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
+    yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
+    return phi[(long long)yy * g.pitch + xx];
+  };
+  const float ph = at(0, 0);
+  const float lap = (4.0f * (at(1, 0) + at(0, 1) + at(-1, 0) + at(0, -1)) +
+                     (at(1, 1) + at(-1, 1) + at(-1, -1) + at(1, -1)) - 20.0f * ph) * (1.0f / 6.0f);
+  mu[(long long)y * g.pitch + x] = P.four_beta * ph * (ph * ph - P.phi_star2) - P.kappa * lap;
+}
+
+// Post-collision-layout state whose pull gives f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0):
+// plane a at cell z holds the equilibrium of direction a at z + e_a, or, when that link leaves
+// through a wall, the equilibrium of the reversed direction at z itself.
+__global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx) return;
+  const float* phi = fields;
+  const float* ux = fields + 2 * g.plane;
+  const float* uy = fields + 3 * g.plane;
+  const float* pp = fields + 4 * g.plane;
+  const float* mu = fields + 5 * (long long)g.plane;
+  const long long cell = (long long)y * g.pitch + x;
+#pragma unroll
+  for (int a = 0; a < Q; ++a) {
+    int xw = x + cx(a), yw = y + cy(a);
+    int b = a;
+    bool hit = false;
+    if (xw < 0 || xw >= g.nx) {
+      if (g.bc_x == BC_WALL) hit = true; else xw = wrap(xw, g.nx);
+    }
+    if (yw < 0 || yw >= g.ny) {
+      if (g.bc_y == BC_WALL) hit = true; else yw = wrap(yw, g.ny);
+    }
+    if (hit) {
+      xw = x;
+      yw = y;
+      b = opp(a);
+    }
+    const long long c = (long long)yw * g.pitch + xw;
+    const float ph = phi[c], u = ux[c], v = uy[c], p = pp[c], m = mu[c];
+    const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
+    const float rho = P.rho_B + cl * P.drho;
+    const float uu15 = 1.5f * (u * u + v * v);
+    const float w = wgt(b);
+    const float eu = (float)cx(b) * u + (float)cy(b) * v;
+    const float poly = 3.0f * eu + 4.5f * eu * eu - uu15;
+    const float geq = w * p + rho * (1.0f / 3.0f) * (w * poly);
+    if (b == 0) {
+      // f_0^eq = phi - sum_{k>0} f^eq_k, kept as the float pair (hi, lo)
+      float rest = 0.0f;
+#pragma unroll
+      for (int k = 1; k < Q; ++k) {
+        const float ek = (float)cx(k) * u + (float)cy(k) * v;
+        rest += wgt(k) * (P.three_gamma_f * m + ph * (3.0f * ek + 4.5f * ek * ek - uu15));
+      }
+      float hi, lo;
+      two_sum(ph, -rest, hi, lo);
+      g.dst[cell] = hi;
+      g.dst[(long long)PLANE_F0LO * g.plane + cell] = lo;
+    } else {
+      g.dst[(long long)a * g.plane + cell] = w * (P.three_gamma_f * m + ph * poly);
+    }
+    g.dst[(long long)(Q + a) * g.plane + cell] = geq;
+  }
+}
+
+cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
+  Grid g = make_grid(s, nullptr, s->buf[s->cur]);
+  dim3 blk(128), grd((s->nx + 127) / 128, s->ny);
+  k_init_mu<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_init_pop<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ FP64 diagnostics
+// Stage 1: one block per row, fixed per-thread stride and fixed tree -> 12 partials per row.
+// Stage 2: one block folds the rows in a fixed order.  Results are bitwise reproducible.
+
+constexpr int DIAG_T = 256;
+
+__device__ __forceinline__ void tree_sum(double* sh, int t) {
+  for (int s = DIAG_T / 2; s > 0; s >>= 1) {
+    if (t < s) sh[t] += sh[t + s];
+    __syncthreads();
+  }
+}
+__device__ __forceinline__ void tree_max(double* sh, int t) {
+  for (int s = DIAG_T / 2; s > 0; s >>= 1) {
+    if (t < s) {
+      const double a = sh[t], b = sh[t + s];
+      sh[t] = (a >= b || a != a) ? a : b;   // NaN propagates
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(DIAG_T) k_diag_rows(Phys P, Grid g, const float* __restrict__ fields,
+                                                      double* __restrict__ part) {
+  __shared__ double sh[DIAG_PARTIALS][DIAG_T];
+  const int y = blockIdx.x, t = threadIdx.x;
+  const float* phi = fields + (long long)y * g.pitch;
+  const float* ux = fields + 2 * g.plane + (long long)y * g.pitch;
+  const float* uy = fields + 3 * g.plane + (long long)y * g.pitch;
+  const float* pp = fields + 4 * g.plane + (long long)y * g.pitch;
+  double acc[DIAG_PARTIALS] = {0};
+  const double phs = P.phi_star;
+  for (int x = t; x < g.nx; x += DIAG_T) {
+    const double ph = phi[x], u = ux[x], v = uy[x], p = pp[x];
+    double c = (ph + phs) / (2.0 * phs);
+    c = c < 0.0 ? 0.0 : (c > 1.0 ? 1.0 : c);
+    acc[0] += ph;
+    acc[1] += c;
+    acc[2] += c * x;
+    acc[3] += c * y;
+    acc[4] += c * u;
+    acc[5] += c * v;
+    const double um = sqrt(u * u + v * v);
+    if (!(um <= acc[6])) acc[6] = um;
+    if (ph > 0.9 * phs) { acc[7] += p; acc[8] += 1.0; }
+    if (ph < -0.9 * phs) { acc[9] += p; acc[10] += 1.0; }
+  }
+  for (int k = 0; k < 11; ++k) sh[k][t] = acc[k];
+  __syncthreads();
+  for (int k = 0; k < 11; ++k) {
+    if (k == 6) tree_max(sh[k], t); else tree_sum(sh[k], t);
+  }
+  if (t < 11) part[(long long)y * DIAG_PARTIALS + t] = sh[t][0];
+  if (t == 11) part[(long long)y * DIAG_PARTIALS + 11] = 0.0;
+}
+
+__global__ void __launch_bounds__(DIAG_T) k_diag_final(Grid g, const double* __restrict__ part,
+                                                       double* __restrict__ out, long long step) {
+  __shared__ double sh[DIAG_PARTIALS][DIAG_T];
+  const int t = threadIdx.x;
+  double acc[DIAG_PARTIALS] = {0};
+  for (int y = t; y < g.ny; y += DIAG_T) {
+    const double* r = part + (long long)y * DIAG_PARTIALS;
+    for (int k = 0; k < 11; ++k) {
+      if (k == 6) {
+        if (!(r[6] <= acc[6])) acc[6] = r[6];
+      } else {
+        acc[k] += r[k];
+      }
+    }
+    if (!(r[1] <= acc[11])) acc[11] = r[1];   // widest liquid chord
+  }
+  for (int k = 0; k < DIAG_PARTIALS; ++k) sh[k][t] = acc[k];
+  __syncthreads();
+  for (int k = 0; k < DIAG_PARTIALS; ++k) {
+    if (k == 6 || k == 11) tree_max(sh[k], t); else tree_sum(sh[k], t);
+  }
+  if (t == 0) {
+    lbm_diag d;
+    d.step = step;
+    d.sum_phi = sh[0][0];
+    d.liquid_area = sh[1][0];
+    const double sc = sh[1][0];
+    d.centroid_x = sc > 0 ? sh[2][0] / sc : 0.0;
+    d.centroid_y = sc > 0 ? sh[3][0] / sc : 0.0;
+    d.vel_x = sc > 0 ? sh[4][0] / sc : 0.0;
+    d.vel_y = sc > 0 ? sh[5][0] / sc : 0.0;
+    d.spread_radius = 0.5 * sh[11][0];
+    d.max_u = sh[6][0];
+    d.p_liquid = sh[8][0] > 0 ? sh[7][0] / sh[8][0] : 0.0;
+    d.p_gas = sh[10][0] > 0 ? sh[9][0] / sh[10][0] : 0.0;
+    d.finite = isfinite(d.sum_phi) && isfinite(d.max_u);
+    d.pad = 0;
+    *reinterpret_cast<lbm_diag*>(out) = d;
+  }
+}
+
+cudaError_t launch_diag(const lbm_sim* s, cudaStream_t st) {
+  Grid g = make_grid(s, nullptr, nullptr);
+  k_diag_rows<<<s->ny, DIAG_T, 0, st>>>(s->phys, g, s->fields, s->red);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_diag_final<<<1, DIAG_T, 0, st>>>(g, s->red, s->red + (long long)s->ny * DIAG_PARTIALS, s->steps);
+  return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same seeded inputs.
+
+Error metric: relative L-infinity, max|gpu - ref| / max|ref|; for the velocity the denominator
+is at least the capillary velocity sigma / (rho_A nu_A) (a static droplet's velocity is a
+spurious current far below any physical scale).  FP32 tolerance: 1e-5 on phi, u and p.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1110_5004_gb300 import build
+    build.build()
+    import paper_1110_5004_gb300 as m
+    return m
+
+
+def rel_errors(got, ref, w):
+    u_cap = w.phys.sigma / (w.phys.rho_A * w.phys.nu_A)
+    out = {}
+    for k in ("phi", "rho", "ux", "uy", "p"):
+        den = np.abs(ref[k]).max()
+        if k in ("ux", "uy"):
+            den = max(np.abs(ref["ux"]).max(), np.abs(ref["uy"]).max(), u_cap)
+        den = max(den, 1e-30)
+        out[k] = float(np.abs(got[k].astype(np.float64) - ref[k]).max() / den)
+    return out
+
+
+def assert_parity(got, ref, w, tol=TOL):
+    err = rel_errors(got, ref, w)
+    bad = {k: v for k, v in err.items() if not v <= tol}
+    assert not bad, "rel L-inf above %g: %r (all %r)" % (tol, bad, err)
+    return err
+
+
+def run_both(lbm, w, steps, tile=None):
+    sim = lbm.Sim.from_workload(w, tile=tile)
+    sim.step(steps)
+    got = sim.moments()
+    ref = oracle.run(w, steps=steps).moments()
+    return sim, got, ref
+
+
+CASES = [
+    # nx, ny, bc_x, bc_y, remove_Fa, gravity, seed
+    (24, 20, W.PERIODIC, W.PERIODIC, 0, 0.0, 1),
+    (24, 20, W.PERIODIC, W.PERIODIC, 1, 0.0, 1),
+    (33, 17, W.PERIODIC, W.WALL, 0, 1e-5, 2),
+    (33, 17, W.PERIODIC, W.WALL, 1, 1e-5, 2),
+    (29, 31, W.WALL, W.WALL, 1, 2e-5, 3),
+    (7, 5, W.PERIODIC, W.PERIODIC, 1, 0.0, 4),
+    (130, 9, W.WALL, W.PERIODIC, 0, 0.0, 5),
+]
+
+
+@pytest.mark.parametrize("nx,ny,bcx,bcy,rf,g,seed", CASES)
+def test_small_grids_200_steps(lbm, nx, ny, bcx, bcy, rf, g, seed):
+    w = W.random_small(nx, ny, seed=seed, bc_x=bcx, bc_y=bcy, remove_Fa=rf, gravity=g)
+    _, got, ref = run_both(lbm, w, 200)
+    assert_parity(got, ref, w)
+
+
+def test_initial_state_moments(lbm):
+    """t = 0: the moments of the initial populations (init kernel) match the oracle's."""
+    w = W.random_small(45, 38, seed=9, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    _, got, ref = run_both(lbm, w, 0)
+    assert_parity(got, ref, w)
+
+
+@pytest.mark.parametrize("tile", [(64, 1), (64, 7), (128, 16), (256, 64), (128, 1000)])
+def test_many_tiles_and_ragged_tails(lbm, tile):
+    """A grid spanning several strips and segments with ragged last tiles (walls and gravity)."""
+    w = W.random_small(300, 70, seed=12, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    _, got, ref = run_both(lbm, w, 60, tile=tile)
+    assert_parity(got, ref, w)
+
+
+def test_tile_shape_does_not_change_results(lbm):
+    """Per-cell arithmetic is independent of the tile shape: bitwise-identical states."""
+    w = W.random_small(150, 44, seed=21, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    outs = []
+    for tile in ((64, 5), (128, 16), (256, 64), (128, 44)):
+        s = lbm.Sim.from_workload(w, tile=tile)
+        s.step(37)
+        outs.append(s.moments())
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
+
+
+@pytest.mark.parametrize("rf", [0, 1])
+def test_c1_static_droplet(lbm, rf):
+    """c1 (128x128 periodic, R = 25, rho 1:0.1): 1e-5 after 200 steps; the full 1000-step run
+    stays within tolerance too."""
+    w = W.static_droplet(remove_Fa=rf)
+    sim = lbm.Sim.from_workload(w)
+    ref = oracle.Sim.from_workload(w)
+    sim.step(200)
+    ref.step(200)
+    assert_parity(sim.moments(), ref.moments(), w)
+    sim.step(800)
+    ref.step(800)
+    assert_parity(sim.moments(), ref.moments(), w)
+    dg, dr = sim.diagnostics(), ref.diagnostics()
+    assert dg["step"] == dr["step"] == 1000
+    assert dg["sum_phi"] == pytest.approx(dr["sum_phi"], rel=1e-6)
+    assert dg["centroid_x"] == pytest.approx(dr["centroid_x"], rel=1e-6)
+    assert dg["spread_radius"] == pytest.approx(dr["spread_radius"], rel=1e-5)
+    assert dg["p_liquid"] == pytest.approx(dr["p_liquid"], rel=1e-5)
+
+
+def test_c2_falling_droplet_until_divergence(lbm):
+    """c2 (256x1024, walls, rho 1:0.01): parity while finite; both sides diverge (the
+    central-difference scheme's density-ratio limit) at the same step."""
+    w = W.falling_droplet()
+    sim = lbm.Sim.from_workload(w)
+    ref = oracle.Sim.from_workload(w)
+    sim.step(30)
+    ref.step(30)
+    assert_parity(sim.moments(), ref.moments(), w, tol=1e-4)
+    first = {}
+    for k in range(30, 80):
+        for name, s in (("gpu", sim), ("ref", ref)):
+            if name not in first and not s.diagnostics()["finite"]:
+                first[name] = k
+        sim.step(1)
+        ref.step(1)
+    assert "gpu" in first and "ref" in first
+    assert abs(first["gpu"] - first["ref"]) <= 2
+
+
+def test_c3_splash_until_divergence(lbm):
+    """c3 (2048x512, rho 1:0.001, Re 500, We 8000): parity over the first steps at full size;
+    both sides diverge within the first dozen steps."""
+    w = W.splash()
+    sim = lbm.Sim.from_workload(w)
+    ref = oracle.Sim.from_workload(w)
+    sim.step(3)
+    ref.step(3)
+    assert_parity(sim.moments(), ref.moments(), w, tol=1e-4)
+    for _ in range(20):
+        sim.step(1)
+        ref.step(1)
+    assert not sim.diagnostics()["finite"] and not ref.diagnostics()["finite"]
+
+
+def test_diverged_state_reports_error_code(lbm):
+    w = W.splash(nx=256, ny=128, D=50)
+    sim = lbm.Sim.from_workload(w)
+    sim.step(30)
+    with pytest.raises(lbm.LBMError) as e:
+        sim.diagnostics(raise_on_divergence=True)
+    assert e.value.code == lbm.LBM_ERR_DIVERGED
+
+
+def test_diagnostics_match_oracle(lbm):
+    w = W.falling_droplet(nx=96, ny=160, R=20.0, yc=100.0, ratio=10.0, steps=0)
+    sim = lbm.Sim.from_workload(w)
+    ref = oracle.Sim.from_workload(w)
+    sim.step(150)
+    ref.step(150)
+    dg, dr = sim.diagnostics(), ref.diagnostics()
+    for k in ("sum_phi", "liquid_area", "centroid_x", "centroid_y", "spread_radius", "p_liquid", "p_gas"):
+        assert dg[k] == pytest.approx(dr[k], rel=1e-5, abs=1e-9), k
+    for k in ("vel_x", "vel_y", "max_u"):
+        assert dg[k] == pytest.approx(dr[k], rel=1e-4, abs=1e-9), k
+    assert dg["finite"] == 1 and dg["step"] == 150
+
+
+def test_diagnostics_are_bitwise_reproducible(lbm):
+    w = W.random_small(64, 48, seed=2)
+    sim = lbm.Sim.from_workload(w)
+    sim.step(10)
+    a, b = sim.diagnostics(), sim.diagnostics()
+    assert a == b
+
+
+def test_device_pointers_in_and_out(lbm):
+    """Fields may be torch CUDA tensors on both sides of the ABI."""
+    import torch
+    w = W.random_small(40, 24, seed=6, bc_y=W.WALL)
+    s = lbm.Sim(w.nx, w.ny, lbm.params_from_physical(w.phys))
+    dev = {k: torch.from_numpy(getattr(w, k)).cuda() for k in ("phi0", "ux0", "uy0", "p0")}
+    s.init_fields(dev["phi0"], dev["ux0"], dev["uy0"], dev["p0"])
+    s.step(25)
+    out = {k: torch.empty((w.ny, w.nx), device="cuda") for k in ("phi", "rho", "ux", "uy", "p")}
+    s.moments(out)
+    host = lbm.Sim.from_workload(w)
+    host.step(25)
+    h = host.moments()
+    for k in out:
+        assert np.array_equal(out[k].cpu().numpy(), h[k]), k
+
+
+def test_zero_steps_and_null_outputs(lbm):
+    w = W.random_small(16, 16, seed=1)
+    s = lbm.Sim.from_workload(w)
+    s.step(0)
+    assert s.step_count == 0
+    o = {"phi": np.empty((16, 16), np.float32)}
+    s.moments(o)
+    assert np.isfinite(o["phi"]).all()
