@@ -156,6 +156,29 @@ LBM_API const char* lbm_strerror(int code);
 /* Message of the last failed call on this host thread ("" if none). */
 LBM_API const char* lbm_last_error(void);
 
+/* Allocation-free FP64 diagnostics of fields the caller already holds on the device.
+ * The paper has no counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc -- a host application that owns the whole device-memory budget (for example a
+ * server whose pools have reserved it), or a loop that must not take the device-wide
+ * synchronisation of a fresh allocation.  It allocates nothing: the per-row partial sums live
+ * in one fixed file-scope device array of the library (8192 rows x 12 doubles plus the result,
+ * 768 KB, held by every GPU that loads the library until the process exits).
+ *   phi, ux, uy, p  device pointers, row-major nx*ny float32 each (caller-owned, read only);
+ *   ny <= 8192 (larger grids: LBM_ERR_INVALID_ARG with a message), nx >= 1, phi_star > 0;
+ *   step            copied into out->step;
+ *   cuda_stream     stream the two reduction kernels run on (NULL: legacy default stream);
+ *   out             host or device lbm_diag; a host record is filled before return (the stream
+ *                   is synchronised) and LBM_ERR_DIVERGED is returned if the fields are not
+ *                   finite; a device record is written asynchronously.
+ * The reduction is the one lbm_diagnostics performs (same partials, order and result).  The
+ * first call on a device looks up the array's device address with that device current; make
+ * that first call before any stream capture.  All calls share the array: nothing in it has to
+ * start at zero (every partial read is written first by the same call), but two calls whose
+ * kernels overlap on the GPU race on it. */
+LBM_API int lbm_diagnostics_fields_noalloc(const float* phi, const float* ux, const float* uy, const float* p,
+                                           int nx, int ny, double phi_star, long long step, void* cuda_stream,
+                                           lbm_diag* out);
+
 /* ------------------------------------------------------------------ ragged batches
  * A batch advances many independent simulations (different sizes and parameters) with one
  * launch per time step over a work list of tiles from all of them.  Simulations stay owned by

@@ -23,7 +23,7 @@ EXPORTS = (
     "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_destroy", "lbm_step_count", "lbm_set_stream",
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
-    "lbm_batch_destroy",
+    "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc",
 )
 
 
@@ -84,6 +84,8 @@ def load(path: str = LIB_PATH):
         "lbm_batch_size": (ip, [vp]),
         "lbm_batch_bytes": (ctypes.c_size_t, [vp]),
         "lbm_batch_destroy": (ip, [vp]),
+        "lbm_diagnostics_fields_noalloc": (ip, [fp, fp, fp, fp, ip, ip, ctypes.c_double, ctypes.c_longlong, vp,
+                                                ctypes.POINTER(lbm_diag)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
