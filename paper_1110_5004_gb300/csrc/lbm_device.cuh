@@ -94,26 +94,41 @@ __device__ __forceinline__ int wrap(int i, int n) {
 // Mirror about a wall half a cell outside the edge: -1 -> 0, -2 -> 1, n -> n-1.
 __device__ __forceinline__ int mirror(int i, int n) { return i < 0 ? -1 - i : (i >= n ? 2 * n - 1 - i : i); }
 
-// Physical neighbourhood of one cell for the pull gather.
-struct Cell {
-  int xp, yp;            // the cell
-  int xm, xq, ym, yq;    // columns x-1, x+1 and rows y-1, y+1 (wrapped)
-  bool wl, wr, wb, wt;   // x-1 / x+1 / y-1 / y+1 lie beyond a wall
+// Wrap an index that lies within one period of [0, n) (the general case takes a modulo).
+__device__ __forceinline__ int wrap1(int i, int n) {
+  if (i < -n || i >= 2 * n) return wrap(i, n);
+  return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+// Column part of one thread's pull neighbourhood (fixed for the whole tile).
+struct ColNb {
+  int xm, x0, xq;      // physical columns of x-1, x, x+1 (wrapped)
+  bool wl, wr;         // x-1 / x+1 lie beyond a wall
+};
+// Row part of the neighbourhood of one gathered row.
+struct RowNb {
+  int rm, r0, rq;      // element offsets (row * pitch) of rows y-1, y, y+1 (wrapped)
+  bool wb, wt;         // y-1 / y+1 lie beyond a wall
 };
 
-__device__ __forceinline__ Cell make_cell(int xp, int yp, const Grid& g) {
-  Cell c;
-  c.xp = xp;
-  c.yp = yp;
+__device__ __forceinline__ ColNb make_col(int xp, const Grid& g) {
+  ColNb c;
+  c.x0 = xp;
   c.xm = xp == 0 ? g.nx - 1 : xp - 1;
   c.xq = xp == g.nx - 1 ? 0 : xp + 1;
-  c.ym = yp == 0 ? g.ny - 1 : yp - 1;
-  c.yq = yp == g.ny - 1 ? 0 : yp + 1;
   c.wl = g.bc_x == BC_WALL && xp == 0;
   c.wr = g.bc_x == BC_WALL && xp == g.nx - 1;
-  c.wb = g.bc_y == BC_WALL && yp == 0;
-  c.wt = g.bc_y == BC_WALL && yp == g.ny - 1;
   return c;
+}
+
+__device__ __forceinline__ RowNb make_row(int yp, const Grid& g) {
+  RowNb r;
+  r.r0 = yp * g.pitch;
+  r.rm = yp == 0 ? (g.ny - 1) * g.pitch : r.r0 - g.pitch;
+  r.rq = yp == g.ny - 1 ? 0 : r.r0 + g.pitch;
+  r.wb = g.bc_y == BC_WALL && yp == 0;
+  r.wt = g.bc_y == BC_WALL && yp == g.ny - 1;
+  return r;
 }
 
 // Error-free sum of two floats: s + e == a + b exactly (round-to-nearest, no contraction).
@@ -123,22 +138,38 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Pull the 9 pre-collision populations of one distribution (planes base..base+8) at cell c:
+// Pull the 9 pre-collision populations of one distribution (planes starting at `src`):
 // v[a] = P*_a(x - e_a), or P*_opp(a)(x) when x - e_a lies beyond a wall (half-way bounce-back).
-__device__ __forceinline__ void gather9(const float* __restrict__ src, int plane, int pitch, const Cell& c,
-                                        int base, float v[Q]) {
-  const float* __restrict__ s0 = src + base * plane;
-  const int rm = c.ym * pitch, r0 = c.yp * pitch, rq = c.yq * pitch;
+// Cells with no wall neighbour take the branch-free path.
+__device__ __forceinline__ void gather9(const float* __restrict__ src, int plane, const ColNb& c, const RowNb& r,
+                                        float v[Q]) {
+  if (!(c.wl | c.wr | r.wb | r.wt)) {
 #pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    const int ex = cx(a), ey = cy(a);
-    const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && c.wb) || (ey == -1 && c.wt);
-    const int sx = ex == 1 ? c.xm : (ex == -1 ? c.xq : c.xp);
-    const int sr = ey == 1 ? rm : (ey == -1 ? rq : r0);
-    const int i_pull = a * plane + sr + sx;
-    const int i_back = opp(a) * plane + r0 + c.xp;
-    v[a] = __ldg(s0 + (hit ? i_back : i_pull));
+    for (int a = 0; a < Q; ++a) {
+      const int sx = cx(a) == 1 ? c.xm : (cx(a) == -1 ? c.xq : c.x0);
+      const int sr = cy(a) == 1 ? r.rm : (cy(a) == -1 ? r.rq : r.r0);
+      v[a] = __ldg(src + a * plane + sr + sx);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      const int ex = cx(a), ey = cy(a);
+      const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && r.wb) || (ey == -1 && r.wt);
+      const int sx = ex == 1 ? c.xm : (ex == -1 ? c.xq : c.x0);
+      const int sr = ey == 1 ? r.rm : (ey == -1 ? r.rq : r.r0);
+      const int i_pull = a * plane + sr + sx;
+      const int i_back = opp(a) * plane + r.r0 + c.x0;
+      v[a] = __ldg(src + (hit ? i_back : i_pull));
+    }
   }
+}
+
+// e_a . (vx, vy) with the zero and unit components folded at compile time.
+template <int A>
+__device__ __forceinline__ float edot(float vx, float vy) {
+  constexpr int ex = cx(A), ey = cy(A);
+  const float tx = ex == 0 ? 0.0f : (ex > 0 ? vx : -vx);
+  return ey == 0 ? tx : (ex == 0 ? (ey > 0 ? vy : -vy) : (ey > 0 ? tx + vy : tx - vy));
 }
 
 // Per-cell record carried from S2 to S3 in registers.
@@ -146,64 +177,101 @@ struct Rec {
   float phi, mu, rho, ux, uy, Fx, Fy, drx, dry, omega_g;
 };
 
-constexpr int RING_PHI = 8;  // rows a-7..a
-constexpr int RING = 4;      // mu, p
+constexpr int RING = 8;      // rows of phi (hi, lo), mu and p, incl. one mirrored ghost row at a wall
 constexpr int RING_F = 6;    // f rows a-5..a awaiting S3 (thread-private)
 constexpr int NF = Q + 1;    // f_0..f_8 and f_0lo
 
 template <int NT>
 struct Smem {
-  float phi_hi[RING_PHI][NT];
-  float phi_lo[RING_PHI][NT];
+  float phi_hi[RING][NT];
+  float phi_lo[RING][NT];
   float mu[RING][NT];
   float p[RING][NT];
-  float f[RING_F][NF][NT];   // own column only: no barrier needed
-  float g[2][Q][NT];         // own column only
+  float2 f[RING_F][NT][NF / 2];  // own column only (no barrier needed); 64-bit accesses
+  float g[2][Q][NT];             // own column only
 };
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
+
+// One direction of both collisions.  With Gamma_a = omega_a(u) = w_a (1 + poly_a):
+//   g^eq_a = w_a p + rho cs2 (Gamma_a - w_a)
+//   S_a    = (e_a - u).[F Gamma_a - (Gamma_a - w_a) grad psi]
+//          = (e_a.F - u.F) Gamma_a - (e_a.grad psi - u.grad psi) (Gamma_a - w_a)
+//   gbar*_a = gbar_a - omega_g (gbar_a - g^eq_a) + (1 - omega_g/2) S_a
+//   f^eq_a = w_a (3 Gamma_f mu + phi poly_a)  (a > 0),   f*_a = f_a - omega_f (f_a - f^eq_a)
+struct CollideC {
+  float ux, uy, uu15, Fx, Fy, uF, Px, Py, uP, rho3, p, og, keep_g, src_g, of, keep_f, gmu, phi;
+};
+
+template <int A>
+__device__ __forceinline__ void collide_dir(const CollideC& k, const float f[NF], const float gb[Q], float* __restrict__ dst,
+                                            int plane, int cell, float& fsum, float& feqsum) {
+  constexpr float w = wgt(A);
+  const float eu = edot<A>(k.ux, k.uy);
+  const float poly = A == 0 ? -k.uu15 : eu * (3.0f + 4.5f * eu) - k.uu15;
+  const float gmw = w * poly;
+  const float gam = w + gmw;
+  const float geq = w * k.p + k.rho3 * gmw;
+  const float S = A == 0 ? (-k.uF) * gam + k.uP * gmw
+                         : (edot<A>(k.Fx, k.Fy) - k.uF) * gam - (edot<A>(k.Px, k.Py) - k.uP) * gmw;
+  dst[(Q + A) * plane + cell] = k.keep_g * gb[A] + k.og * geq + k.src_g * S;
+  if (A > 0) {
+    const float feq = w * (k.gmu + k.phi * poly);
+    fsum += f[A];
+    feqsum += feq;
+    dst[A * plane + cell] = k.keep_f * f[A] + k.of * feq;
+  }
+}
 
 // Collision of both distributions at one cell and store of the post-collision populations.
 // f[] holds f_0..f_8 and f_0lo (index Q), gb[] gbar_0..gbar_8.
 __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx, float gpy,
                                               const float f[NF], const float gb[Q], float* __restrict__ dst,
                                               int plane, int cell) {
-  const float dpsix = gpx - (1.0f / 3.0f) * r.drx;
-  const float dpsiy = gpy - (1.0f / 3.0f) * r.dry;
-  const float uu15 = 1.5f * (r.ux * r.ux + r.uy * r.uy);
-  const float rho3 = r.rho * (1.0f / 3.0f);
-  const float og = r.omega_g;
-  const float src_g = 1.0f - 0.5f * og;
-  const float of = P.omega_f;
-  const float gmu = P.three_gamma_f * r.mu;
+  CollideC k;
+  k.ux = r.ux;
+  k.uy = r.uy;
+  k.uu15 = 1.5f * (r.ux * r.ux + r.uy * r.uy);
+  k.Fx = r.Fx;
+  k.Fy = r.Fy;
+  k.uF = r.ux * r.Fx + r.uy * r.Fy;
+  k.Px = gpx - (1.0f / 3.0f) * r.drx;   // grad psi = grad p - cs2 grad rho
+  k.Py = gpy - (1.0f / 3.0f) * r.dry;
+  k.uP = r.ux * k.Px + r.uy * k.Py;
+  k.rho3 = r.rho * (1.0f / 3.0f);
+  k.p = p;
+  k.og = r.omega_g;
+  k.keep_g = 1.0f - r.omega_g;
+  k.src_g = 1.0f - 0.5f * r.omega_g;
+  k.of = P.omega_f;
+  k.keep_f = 1.0f - P.omega_f;
+  k.gmu = P.three_gamma_f * r.mu;
+  k.phi = r.phi;
   float fsum = 0.0f, feqsum = 0.0f;
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    const float w = wgt(a);
-    const float ex = (float)cx(a), ey = (float)cy(a);
-    const float eu = ex * r.ux + ey * r.uy;
-    const float poly = 3.0f * eu + 4.5f * eu * eu - uu15;     // omega_a(u)/w_a - 1
-    const float gam = w + w * poly;                            // omega_a(u)
-    const float gmw = w * poly;                                // omega_a(u) - w_a
-    const float geq = w * p + rho3 * gmw;
-    const float S = (ex - r.ux) * (r.Fx * gam - gmw * dpsix) + (ey - r.uy) * (r.Fy * gam - gmw * dpsiy);
-    dst[(Q + a) * plane + cell] = gb[a] - og * (gb[a] - geq) + src_g * S;
-    if (a > 0) {
-      const float feq = w * (gmu + r.phi * poly);
-      fsum += f[a];
-      feqsum += feq;
-      dst[a * plane + cell] = f[a] - of * (f[a] - feq);
-    }
-  }
+  collide_dir<0>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<1>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<2>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<3>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<4>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<5>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<6>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<7>(k, f, gb, dst, plane, cell, fsum, feqsum);
+  collide_dir<8>(k, f, gb, dst, plane, cell, fsum, feqsum);
   // f_0^eq - f_0 = (phi - f_0) - sum_{a>0} f^eq_a = sum_{a>0} (f_a - f^eq_a): small, exact inputs
   float hi, lo;
-  two_sum(f[0], f[Q] + of * (fsum - feqsum), hi, lo);
+  two_sum(f[0], f[Q] + P.omega_f * (fsum - feqsum), hi, lo);
   dst[cell] = hi;
   dst[PLANE_F0LO * plane + cell] = lo;
 }
 
 // The fused step (MODE_STEP) or the moment evaluation (MODE_MOMENTS) over one tile:
 // columns [x0, x0 + tile_w) x rows [ya, yb) of one simulation.
+//
+// Stencils read fixed neighbours (t +- 1, row +- 1) of the shared rings.  Beyond a wall the
+// ghost value is the mirror image of the first/last row or column (zero normal gradient); the
+// thread that computes a value next to a wall also stores it into that ghost slot, so no read
+// is remapped.  Only one ghost row/column is ever read because every stage runs on real cells
+// and the stencils have radius 1.
 template <int NT, int MODE>
 __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const MomentOut& mo, int strip, int seg,
                                          Smem<NT>& sm) {
@@ -217,35 +285,46 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
   const bool xwall = g.bc_x == BC_WALL;
   const bool ywall = g.bc_y == BC_WALL;
   const bool col_real = !xwall || (xl >= 0 && xl < g.nx);
-  const int xp = wrap(xl, g.nx);
+  const int xp = wrap1(xl, g.nx);
   const bool in_w3 = t < width + 6 && col_real;
   const bool in_w2 = t >= 1 && t < width + 5 && col_real;
   const bool in_w1 = t >= 2 && t < width + 4 && col_real;
   const bool in_w0 = t >= 3 && t < width + 3;
-  // shared-memory column of the logical neighbour xl + d (ghost columns beyond a wall read
-  // their mirror image)
-  auto col = [&](int d) {
-    int q = xl + d;
-    if (xwall && (q < 0 || q >= g.nx)) q = mirror(q, g.nx);
-    return q - (x0 - 3);
-  };
-  auto row = [&](int r) { return (ywall && (r < 0 || r >= g.ny)) ? mirror(r, g.ny) : r; };
+  // ghost column this thread also fills (its mirror image beyond a wall), or -1
+  const int tg = (xwall && xl == 0) ? t - 1 : ((xwall && xl == g.nx - 1) ? t + 1 : -1);
+  // ghost row filled together with real row r, or a value no row takes
+  constexpr int NOROW = -1000000;
+  auto ghost_row = [&](int r) { return !ywall ? NOROW : (r == 0 ? -1 : (r == g.ny - 1 ? g.ny : NOROW)); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
-  auto s0_active = [&](int r) { return r >= ya - 3 && r <= yb + 2 && in_w3 && row_ok(r); };
-  auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
-  const int cm = col(-1), c0 = t, cp = col(1);
+  const ColNb cn = make_col(xp, g);
+  const float* __restrict__ srcF = g.src;
+  const float* __restrict__ srcG = g.src + Q * g.plane;
+  const float* __restrict__ srcL = g.src + PLANE_F0LO * g.plane;
+
+  // stores one ring value plus its mirrored ghost copies
+  auto put = [&](float (*ring)[NT], int r, float v) {
+    ring[r & (RING - 1)][t] = v;
+    if (tg >= 0) ring[r & (RING - 1)][tg] = v;
+    const int gr = ghost_row(r);
+    if (gr != NOROW) {
+      ring[gr & (RING - 1)][t] = v;
+      if (tg >= 0) ring[gr & (RING - 1)][tg] = v;
+    }
+  };
 
   // prefetched gathers: f (+ f_0lo) of the next S0 row, gbar of the next S2 row
   float fp[NF], gp[Q];
   auto fetch_f = [&](int r) {
-    const Cell c = make_cell(xp, wrap(r, g.ny), g);
-    gather9(g.src, g.plane, g.pitch, c, 0, fp);
-    fp[Q] = __ldg(g.src + PLANE_F0LO * g.plane + c.yp * g.pitch + c.xp);
+    const RowNb rn = make_row(wrap1(r, g.ny), g);
+    gather9(srcF, g.plane, cn, rn, fp);
+    fp[Q] = __ldg(srcL + rn.r0 + cn.x0);
   };
   auto fetch_g = [&](int r) {
-    const Cell c = make_cell(xp, wrap(r, g.ny), g);
-    gather9(g.src, g.plane, g.pitch, c, Q, gp);
+    const RowNb rn = make_row(wrap1(r, g.ny), g);
+    gather9(srcG, g.plane, cn, rn, gp);
   };
+  auto s0_active = [&](int r) { return r <= yb + 2 && in_w3 && row_ok(r); };
+  auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
   if (s0_active(ya - 3)) fetch_f(ya - 3);
 
   Rec cur{}, prev{};
@@ -256,11 +335,11 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
       const float small = fp[Q] + (((fp[1] + fp[2]) + (fp[3] + fp[4])) + ((fp[5] + fp[6]) + (fp[7] + fp[8])));
       float hi, lo;
       two_sum(fp[0], small, hi, lo);
-      sm.phi_hi[a & (RING_PHI - 1)][t] = hi;
-      sm.phi_lo[a & (RING_PHI - 1)][t] = lo;
+      put(sm.phi_hi, a, hi);
+      put(sm.phi_lo, a, lo);
       if (MODE == MODE_STEP && in_w0 && a >= ya) {
 #pragma unroll
-        for (int k = 0; k < NF; ++k) sm.f[fslot][k][t] = fp[k];
+        for (int k = 0; k < NF / 2; ++k) sm.f[fslot][t][k] = make_float2(fp[2 * k], fp[2 * k + 1]);
       }
     }
     if (s0_active(a + 1)) fetch_f(a + 1);
@@ -268,46 +347,44 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
     {
       const int r = a - 2;
       if (r >= ya - 2 && r <= yb + 1 && in_w2 && row_ok(r)) {
-        const float* hs = sm.phi_hi[row(r - 1) & (RING_PHI - 1)];
-        const float* h0 = sm.phi_hi[r & (RING_PHI - 1)];
-        const float* hn = sm.phi_hi[row(r + 1) & (RING_PHI - 1)];
-        const float* ls = sm.phi_lo[row(r - 1) & (RING_PHI - 1)];
-        const float* l0 = sm.phi_lo[r & (RING_PHI - 1)];
-        const float* ln = sm.phi_lo[row(r + 1) & (RING_PHI - 1)];
-        const float H = h0[c0], L = l0[c0];
+        const float* hs = sm.phi_hi[(r - 1) & (RING - 1)];
+        const float* h0 = sm.phi_hi[r & (RING - 1)];
+        const float* hn = sm.phi_hi[(r + 1) & (RING - 1)];
+        const float* ls = sm.phi_lo[(r - 1) & (RING - 1)];
+        const float* l0 = sm.phi_lo[r & (RING - 1)];
+        const float* ln = sm.phi_lo[(r + 1) & (RING - 1)];
+        const float H = h0[t], L = l0[t];
         // differences from the centre: exact for neighbouring values of like magnitude
         auto d = [&](const float* hr, const float* lr, int c) { return (hr[c] - H) + (lr[c] - L); };
-        const float lap = (4.0f * ((d(h0, l0, cp) + d(hn, ln, c0)) + (d(h0, l0, cm) + d(hs, ls, c0))) +
-                           ((d(hn, ln, cp) + d(hn, ln, cm)) + (d(hs, ls, cm) + d(hs, ls, cp)))) * (1.0f / 6.0f);
+        const float lap = (4.0f * ((d(h0, l0, t + 1) + d(hn, ln, t)) + (d(h0, l0, t - 1) + d(hs, ls, t))) +
+                           ((d(hn, ln, t + 1) + d(hn, ln, t - 1)) + (d(hs, ls, t - 1) + d(hs, ls, t + 1)))) *
+                          (1.0f / 6.0f);
         const float ph = H + L;
         const float dm = (H - P.phi_star) + L, dp = (H + P.phi_star) + L;
-        sm.mu[r & (RING - 1)][t] = P.four_beta * ph * dm * dp - P.kappa * lap;
+        put(sm.mu, r, P.four_beta * ph * dm * dp - P.kappa * lap);
       }
     }
     // ---- S2: u, p at row a-4
     {
       const int r = a - 4;
       if (s2_active(r)) {
-        const int rs_ = row(r - 1) & (RING_PHI - 1), r0_ = r & (RING_PHI - 1), rn_ = row(r + 1) & (RING_PHI - 1);
-        const float* hs = sm.phi_hi[rs_];
-        const float* h0 = sm.phi_hi[r0_];
-        const float* hn = sm.phi_hi[rn_];
-        const float* ls = sm.phi_lo[rs_];
-        const float* l0 = sm.phi_lo[r0_];
-        const float* ln = sm.phi_lo[rn_];
-        const float* ms = sm.mu[row(r - 1) & (RING - 1)];
+        const float* hs = sm.phi_hi[(r - 1) & (RING - 1)];
+        const float* h0 = sm.phi_hi[r & (RING - 1)];
+        const float* hn = sm.phi_hi[(r + 1) & (RING - 1)];
+        const float* l0 = sm.phi_lo[r & (RING - 1)];
+        const float* ms = sm.mu[(r - 1) & (RING - 1)];
         const float* m0 = sm.mu[r & (RING - 1)];
-        const float* mn = sm.mu[row(r + 1) & (RING - 1)];
-        auto D = [&](const float* ha, const float* la, int ca, const float* hb, const float* lb, int cb) {
-          return (ha[ca] - hb[cb]) + (la[ca] - lb[cb]);
-        };
-        const float ph = h0[c0] + l0[c0];
-        const float gphx = (4.0f * D(h0, l0, cp, h0, l0, cm) + (D(hn, ln, cp, hn, ln, cm) + D(hs, ls, cp, hs, ls, cm))) *
+        const float* mn = sm.mu[(r + 1) & (RING - 1)];
+        // grad phi only feeds grad rho (density and pressure terms): the high words suffice
+        const float ph = h0[t] + l0[t];
+        const float gphx = (4.0f * (h0[t + 1] - h0[t - 1]) + ((hn[t + 1] - hn[t - 1]) + (hs[t + 1] - hs[t - 1]))) *
                            (1.0f / 12.0f);
-        const float gphy = (4.0f * D(hn, ln, c0, hs, ls, c0) + (D(hn, ln, cp, hs, ls, cp) + D(hn, ln, cm, hs, ls, cm))) *
+        const float gphy = (4.0f * (hn[t] - hs[t]) + ((hn[t + 1] - hs[t + 1]) + (hn[t - 1] - hs[t - 1]))) *
                            (1.0f / 12.0f);
-        const float gmx = (4.0f * (m0[cp] - m0[cm]) + (mn[cp] - mn[cm] - ms[cm] + ms[cp])) * (1.0f / 12.0f);
-        const float gmy = (4.0f * (mn[c0] - ms[c0]) + (mn[cp] + mn[cm] - ms[cm] - ms[cp])) * (1.0f / 12.0f);
+        const float gmx = (4.0f * (m0[t + 1] - m0[t - 1]) + ((mn[t + 1] - mn[t - 1]) + (ms[t + 1] - ms[t - 1]))) *
+                          (1.0f / 12.0f);
+        const float gmy = (4.0f * (mn[t] - ms[t]) + ((mn[t + 1] - ms[t + 1]) + (mn[t - 1] - ms[t - 1]))) *
+                          (1.0f / 12.0f);
         const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
         const float rho = P.rho_B + cl * P.drho;
         const float fsx = -ph * gmx;
@@ -315,20 +392,21 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
         const float gy = -rho * P.gravity;
         float sdef = 0.0f;
         if (P.remove_Fa) {
-          const float lmu = (4.0f * (m0[cp] + mn[c0] + m0[cm] + ms[c0]) + (mn[cp] + mn[cm] + ms[cm] + ms[cp]) -
-                             20.0f * m0[c0]) * (1.0f / 6.0f);
+          const float lmu = (4.0f * (m0[t + 1] + mn[t] + m0[t - 1] + ms[t]) + (mn[t + 1] + mn[t - 1] + ms[t - 1] + ms[t + 1]) -
+                             20.0f * m0[t]) * (1.0f / 6.0f);
           sdef = P.s_coef * lmu;
         }
         const float* gb = gp;
         const float m0g = ((gb[0] + gb[1]) + (gb[2] + gb[3])) + ((gb[4] + gb[5]) + (gb[6] + gb[7])) + gb[8];
         const float jx = (gb[1] - gb[3]) + (gb[5] - gb[6]) + (gb[8] - gb[7]);
         const float jy = (gb[2] - gb[4]) + (gb[5] + gb[6]) - (gb[7] + gb[8]);
-        const float denom = P.remove_Fa ? rho - 0.5f * sdef : rho;
-        const float ux = (3.0f * jx + 0.5f * fsx) / denom;
-        const float uy = (3.0f * jy + 0.5f * (fsy + gy)) / denom;
+        const float rrho = __fdividef(1.0f, rho);
+        const float rden = P.remove_Fa ? __fdividef(1.0f, rho - 0.5f * sdef) : rrho;
+        const float ux = (3.0f * jx + 0.5f * fsx) * rden;
+        const float uy = (3.0f * jy + 0.5f * (fsy + gy)) * rden;
         const float drx = P.rho_prime * gphx, dry = P.rho_prime * gphy;
         const float p = m0g + (1.0f / 6.0f) * (ux * drx + uy * dry);
-        sm.p[r & (RING - 1)][t] = p;
+        put(sm.p, r, p);
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && r >= ya && r < yb) {
             const int o = r * g.pitch + xp;
@@ -344,7 +422,7 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
             for (int k = 0; k < Q; ++k) sm.g[r & 1][k][t] = gb[k];
           }
           cur.phi = ph;
-          cur.mu = m0[c0];
+          cur.mu = m0[t];
           cur.rho = rho;
           cur.ux = ux;
           cur.uy = uy;
@@ -353,7 +431,7 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
           cur.drx = drx;
           cur.dry = dry;
           const float muv = P.mu_B + cl * (P.mu_A - P.mu_B);
-          cur.omega_g = 1.0f / (3.0f * muv / rho + 0.5f);
+          cur.omega_g = __fdividef(1.0f, 3.0f * muv * rrho + 0.5f);   // 1 / tau_g(phi)
         }
       }
       if (s2_active(r + 1)) fetch_g(r + 1);
@@ -363,18 +441,24 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
     if (MODE == MODE_STEP) {
       const int r = a - 5;
       if (r >= ya && r < yb && in_w0) {
-        const float* qs = sm.p[row(r - 1) & (RING - 1)];
+        const float* qs = sm.p[(r - 1) & (RING - 1)];
         const float* q0 = sm.p[r & (RING - 1)];
-        const float* qn = sm.p[row(r + 1) & (RING - 1)];
-        const float gpx = (4.0f * (q0[cp] - q0[cm]) + (qn[cp] - qn[cm] - qs[cm] + qs[cp])) * (1.0f / 12.0f);
-        const float gpy = (4.0f * (qn[c0] - qs[c0]) + (qn[cp] + qn[cm] - qs[cm] - qs[cp])) * (1.0f / 12.0f);
+        const float* qn = sm.p[(r + 1) & (RING - 1)];
+        const float gpx = (4.0f * (q0[t + 1] - q0[t - 1]) + ((qn[t + 1] - qn[t - 1]) + (qs[t + 1] - qs[t - 1]))) *
+                          (1.0f / 12.0f);
+        const float gpy = (4.0f * (qn[t] - qs[t]) + ((qn[t + 1] - qs[t + 1]) + (qn[t - 1] - qs[t - 1]))) *
+                          (1.0f / 12.0f);
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
         float f[NF], gb[Q];
 #pragma unroll
-        for (int k = 0; k < NF; ++k) f[k] = sm.f[rslot][k][t];
+        for (int k = 0; k < NF / 2; ++k) {
+          const float2 v = sm.f[rslot][t][k];
+          f[2 * k] = v.x;
+          f[2 * k + 1] = v.y;
+        }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
-        collide_store(P, prev, q0[c0], gpx, gpy, f, gb, g.dst, g.plane, r * g.pitch + xp);
+        collide_store(P, prev, q0[t], gpx, gpy, f, gb, g.dst, g.plane, r * g.pitch + xp);
       }
     }
     prev = cur;

@@ -4,7 +4,7 @@
 #include <stddef.h>
 #include <string>
 
-#include "../../include/lbm.h"
+#include "lbm.h"  // include/ is on the include path
 #include "lbm_device.cuh"
 
 struct lbm_sim {
