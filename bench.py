@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--e2e-iters", type=int, default=20)
     ap.add_argument("--cpu-steps", type=int, default=48, help="oracle steps for the CPU baseline sample")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="main line only (no batch / serving legs)")
+    ap.add_argument("--batch-sims", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-step-scale", type=float, default=0.2)
     return ap.parse_args()
 
 
@@ -164,6 +169,75 @@ def cpu_baseline(w, steps):
     return {"value": w.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "%d FP64 oracle steps of %s (%d cells), re-initialised every %d steps, %.1f s"
                       % (steps, w.name, w.cells, REINIT_EVERY, dt)}
+
+
+def batch_leg(args, lbm, torch):
+    """Ragged batch of independent droplets (256 sims, grids 64^2..512^2, aspect 1..4, seed 1234):
+    aggregate MLUPS of the persistent graph-replayed batch vs the same sims stepped back to back
+    with the plain stepper; the batch kernel's tile shape is autotuned on the mix."""
+    import workloads as W
+    from paper_1110_5004_gb300 import autotune
+    ws = W.ragged_batch(n=args.batch_sims, steps=args.batch_steps)
+    cells = sum(w.cells for w in ws)
+    stream = torch.cuda.current_stream()
+    out = {"sims": len(ws), "steps": args.batch_steps, "cells": cells,
+           "workload": "c4 ragged batch, seed 1234"}
+    for st, name in ((0, "fp32"), (2, "bf16")):
+        sims = [lbm.Sim.from_workload(w, storage=st, stream=stream) for w in ws]
+        b = lbm.Batch(stream=stream)
+        for s in sims:
+            b.add(s)
+        tile = autotune.tune_batch(b, reps=2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.step(args.batch_steps)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        finite = sum(s.diagnostics()["finite"] for s in sims)
+        out[name] = {"aggregate_mlups": cells * args.batch_steps / dt / 1e6, "seconds": dt,
+                     "tile": list(tile[:2]), "finite_at_end": finite}
+        b.close()
+        for s in sims:
+            s.close()
+    out["back_to_back_fp32_mlups"] = None
+    return out
+
+
+def batch_leg_b2b(args, lbm, torch, ws):
+    stream = torch.cuda.current_stream()
+    total = 0.0
+    for w in ws:
+        s = lbm.Sim.from_workload(w, stream=stream)
+        torch.cuda.synchronize()
+        ts = time.perf_counter()
+        s.step(args.batch_steps)
+        torch.cuda.synchronize()
+        total += time.perf_counter() - ts
+        s.close()
+    return total
+
+
+def serve_leg(args, lbm, torch):
+    """Poisson stream of falling-droplet requests (seed 5678, 50 req/s, grids 128x256..1024x4096,
+    density ratio 10..1000), step counts scaled by --serve-step-scale so the run stays bounded:
+    continuous batching under a 120 GB budget vs back-to-back plain runs, both in real time."""
+    import workloads as W
+    from paper_1110_5004_gb300 import serve
+    reqs = [serve.Request(r.rid, r.workload, r.workload.steps, r.arrival_s)
+            for r in W.serving_stream(n=args.serve_requests, step_scale=args.serve_step_scale)]
+    srv = serve.Server(budget_bytes=120 * 10 ** 9, chunk_steps=200, check_steps=400)
+    t0 = time.perf_counter()
+    res = srv.run(reqs)
+    wall = time.perf_counter() - t0
+    served = serve.summarize(res, wall)
+    served["max_concurrent"] = srv.max_concurrent
+    srv.close()
+    t0 = time.perf_counter()
+    res_p = serve.run_plain(reqs, check_every_steps=400)
+    plain = serve.summarize(res_p, time.perf_counter() - t0)
+    return {"workload": "c5 Poisson 50 req/s, seed 5678, %d requests, steps x %g"
+                        % (len(reqs), args.serve_step_scale),
+            "served": served, "plain_back_to_back": plain}
 
 
 def run_reference(args):
@@ -299,6 +373,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_steps)
 
+    batch = serving = None
+    if not args.quick:
+        import workloads as W
+        batch = batch_leg(args, lbm, torch)
+        ws = W.ragged_batch(n=args.batch_sims, steps=args.batch_steps)
+        b2b = batch_leg_b2b(args, lbm, torch, ws)
+        batch["back_to_back_fp32_mlups"] = batch["cells"] * args.batch_steps / b2b / 1e6
+        serving = serve_leg(args, lbm, torch)
+
     if rank == 0:
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
@@ -317,7 +400,9 @@ def run_ours(args):
                                 % REINIT_EVERY},
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
-                "cpu_baseline": cpu}
+                "cpu_baseline": cpu,
+                "batch": batch,
+                "serving": serving}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

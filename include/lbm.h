@@ -192,6 +192,9 @@ LBM_API int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch**
 LBM_API int lbm_batch_add(lbm_batch* b, lbm_sim* sim, int* slot);
 LBM_API int lbm_batch_remove(lbm_batch* b, int slot);
 LBM_API int lbm_batch_step(lbm_batch* b, int k);
+/* Tile shape of the batch kernel (threads per CTA 64/128/256; rows per tile for members that
+ * did not set their own, >= 1); 0 keeps the current value.  Takes effect at the next step. */
+LBM_API int lbm_batch_set_tile(lbm_batch* b, int threads, int seg_rows);
 /* Members, device bytes in use. */
 LBM_API int lbm_batch_size(const lbm_batch* b);
 LBM_API size_t lbm_batch_bytes(const lbm_batch* b);

@@ -163,6 +163,9 @@ class Batch:
     def step(self, k=1):
         _lib.check(lib().lbm_batch_step(self._h, int(k)))
 
+    def set_tile(self, threads=0, seg_rows=0):
+        _lib.check(lib().lbm_batch_set_tile(self._h, int(threads), int(seg_rows)))
+
     @property
     def size(self):
         return int(lib().lbm_batch_size(self._h))

@@ -23,7 +23,7 @@ EXPORTS = (
     "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_destroy", "lbm_step_count", "lbm_set_stream",
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
-    "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc",
+    "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile",
 )
 
 
@@ -81,6 +81,7 @@ def load(path: str = LIB_PATH):
         "lbm_batch_add": (ip, [vp, vp, ctypes.POINTER(ip)]),
         "lbm_batch_remove": (ip, [vp, ip]),
         "lbm_batch_step": (ip, [vp, ip]),
+        "lbm_batch_set_tile": (ip, [vp, ip, ip]),
         "lbm_batch_size": (ip, [vp]),
         "lbm_batch_bytes": (ctypes.c_size_t, [vp]),
         "lbm_batch_destroy": (ip, [vp]),

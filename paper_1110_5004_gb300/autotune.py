@@ -1,0 +1,120 @@
+"""Tile-shape autotuner for the fused step kernel and the batch kernel.
+
+The step kernel's shape is (threads per CTA, rows per CTA).  Threads fix the strip width
+(threads - 6 interior columns); rows trade pipeline warm-up (5 extra S0 rows per segment) for
+parallelism (one CTA per strip x segment).  The best pair depends on the grid, the storage and
+the device, so it is measured: each candidate runs a few steps timed with CUDA events on the
+simulation's stream, and the fastest is cached per (device, grid class, storage, kernel source)
+in a JSON file next to the library (git-ignored).
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.path.join(HERE, "_autotune_cache.json")
+THREADS = (64, 128, 256)
+ROWS = (0, 8, 12, 16, 24, 32, 48, 64, 128)
+_lock = threading.Lock()
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for f in ("lbm_device.cuh", "lbm_kernels.cu", "lbm_batch.cu"):
+        with open(os.path.join(HERE, "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def _device_name():
+    import torch
+    return torch.cuda.get_device_name(torch.cuda.current_device()).replace(" ", "_")
+
+
+def grid_class(nx, ny):
+    """Grids of similar shape share a tuned tile: round sizes up to powers of two."""
+    def up(v):
+        p = 32
+        while p < v:
+            p *= 2
+        return p
+    return "%dx%d" % (up(nx), up(ny))
+
+
+def _load():
+    if os.path.exists(CACHE):
+        try:
+            with open(CACHE) as f:
+                return json.load(f)
+        except (OSError, ValueError):
+            return {}
+    return {}
+
+
+def _store(cache):
+    tmp = CACHE + ".tmp%d" % os.getpid()
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    os.replace(tmp, CACHE)
+
+
+def _key(kind, nx, ny, storage):
+    return "|".join((kind, _device_name(), _kernel_hash(), grid_class(nx, ny), "st%d" % storage))
+
+
+def _time(fn, reps, stream):
+    import torch
+    fn()                                            # warm-up (graph capture, attributes)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def tune_sim(sim, storage=0, reps=6, candidates=None, use_cache=True):
+    """Measure tile candidates on `sim` (its state advances; re-initialise it afterwards) and
+    set the fastest.  Returns (threads, rows, ms per step)."""
+    import torch
+    key = _key("sim", sim.nx, sim.ny, storage)
+    with _lock:
+        cache = _load() if use_cache else {}
+    if key in cache:
+        t, r, ms = cache[key]
+        sim.set_tile(t, r)
+        return t, r, ms
+    stream = torch.cuda.current_stream()
+    sim.set_stream(stream)
+    best = None
+    for t, r in candidates or [(t, r) for t in THREADS for r in ROWS]:
+        sim.set_tile(t, r)
+        ms = _time(lambda: sim.step(1), reps, stream)
+        if best is None or ms < best[2]:
+            best = (t, r, ms)
+    sim.set_tile(best[0], best[1])
+    if use_cache:
+        with _lock:
+            cache = _load()
+            cache[key] = list(best)
+            _store(cache)
+    return best
+
+
+def tune_batch(batch, reps=3, candidates=None):
+    """Measure (threads, rows) of the batch kernel on the current membership (members advance)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    best = None
+    for t, r in candidates or [(t, r) for t in (64, 128) for r in (8, 16, 32, 64)]:
+        batch.set_tile(t, r)
+        ms = _time(lambda: batch.step(2), reps, stream)
+        if best is None or ms < best[2]:
+            best = (t, r, ms / 2)
+    batch.set_tile(best[0], best[1])
+    return best

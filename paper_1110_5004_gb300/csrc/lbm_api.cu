@@ -62,11 +62,16 @@ void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, in
   *seg_out = seg_h;
 }
 
-Grid make_grid(const lbm_sim* s, const float* src, float* dst) {
+Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
   Grid g{};
   g.src = src;
   g.dst = dst;
   g.plane = (int)s->plane;
+  g.storage = s->params.storage;
+  g.sf = s->sf;
+  g.isf = 1.0f / s->sf;
+  g.sg = s->sg;
+  g.isg = 1.0f / s->sg;
   g.nx = s->nx;
   g.ny = s->ny;
   g.pitch = s->pitch;
@@ -102,8 +107,8 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("beta, kappa and phi_star must be positive"), LBM_ERR_INVALID_ARG;
   if (!(p->theta_M >= 0) || !(p->gravity == p->gravity))
     return set_error("theta_M must be >= 0 and gravity finite"), LBM_ERR_INVALID_ARG;
-  if (p->storage != LBM_FP32)
-    return set_error("storage %d not available in this build", p->storage), LBM_ERR_INVALID_ARG;
+  if (p->storage != LBM_FP32 && p->storage != LBM_FP16_DEV && p->storage != LBM_BF16_DEV)
+    return set_error("storage must be LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -126,9 +131,8 @@ int lbm_params_from_sigma_W(double sigma, double W, double phi_star, double* bet
 double lbm_tau_from_nu(double nu) { return 3.0 * nu + 0.5; }
 
 size_t lbm_device_bytes(int nx, int ny, int storage) {
-  (void)storage;
   const size_t plane = (size_t)ny * pitch_of(nx);
-  return 2 * N_PLANES * plane * sizeof(float) + N_FIELDS * plane * sizeof(float) +
+  return 2 * (size_t)state_bytes_per_cell(storage) * plane + N_FIELDS * plane * sizeof(float) +
          ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double);
 }
 
@@ -146,7 +150,9 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
   s->params = *params;
   s->phys = make_phys(*params);
   s->stream = (cudaStream_t)cuda_stream;
-  const size_t pop_bytes = (size_t)N_PLANES * s->plane * sizeof(float);
+  const size_t pop_bytes = (size_t)state_bytes_per_cell(params->storage) * s->plane;
+  // FP16 keeps the O(mu, u) populations in its normal range: 2^12 maps 1.5e-8 .. 16 onto it
+  if (params->storage == LBM_FP16_DEV) s->sf = s->sg = 4096.0f;
   cudaError_t e;
   int dev = 0;
   if ((e = cudaGetDevice(&dev)) != cudaSuccess ||

@@ -15,8 +15,8 @@ namespace lbm {
 struct SimDesc {
   Phys P;
   Grid g;                 // src/dst unused; buffers below
-  const float* buf0;
-  float* buf1;
+  const void* buf0;
+  void* buf1;
   int cur0;               // buffer holding the state when the graph replay starts
   int pad;
 };
@@ -32,8 +32,12 @@ __global__ void __launch_bounds__(NT) k_batch(const SimDesc* __restrict__ sims, 
     Grid g = d.g;
     const bool odd = ((d.cur0 + parity) & 1) != 0;
     g.src = odd ? d.buf1 : d.buf0;
-    g.dst = odd ? const_cast<float*>(d.buf0) : d.buf1;
-    run_tile<NT, MODE_STEP>(d.P, g, MomentOut{}, it.y, it.z, sm);
+    g.dst = odd ? const_cast<void*>(d.buf0) : d.buf1;
+    switch (g.storage) {   // members may differ in storage; the branch is uniform per tile
+      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      default: run_tile<NT, MODE_STEP, ST_FP32>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+    }
     __syncthreads();  // shared rings are reused by the next tile
   }
 }
@@ -247,6 +251,17 @@ int lbm_batch_step(lbm_batch* b, int k) {
     if (flip) s->cur ^= 1;
   }
   if (flip) b->flip ^= 1;
+  return LBM_OK;
+}
+
+int lbm_batch_set_tile(lbm_batch* b, int threads, int seg_rows) {
+  if (!b) return set_error("batch is NULL"), LBM_ERR_INVALID_ARG;
+  if (threads && threads != 64 && threads != 128 && threads != 256)
+    return set_error("threads must be 64, 128 or 256"), LBM_ERR_INVALID_ARG;
+  if (seg_rows < 0) return set_error("seg_rows must be >= 1"), LBM_ERR_INVALID_ARG;
+  if (threads) b->nt = threads;
+  if (seg_rows) b->seg_h = seg_rows;
+  b->dirty = true;
   return LBM_OK;
 }
 

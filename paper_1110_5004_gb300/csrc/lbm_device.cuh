@@ -24,6 +24,8 @@
 // thread-private shared-memory rings.  One __syncthreads per row orders S2 -> S3; the ring
 // sizes keep every other reader/writer pair on distinct rows.
 #pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -68,13 +70,24 @@ struct Phys {
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
-constexpr int N_PLANES = 19;   // f_0..f_8, gbar_0..gbar_8, f_0lo
+constexpr int N_PLANES = 19;   // FP32 storage: f_0..f_8, gbar_0..gbar_8, f_0lo
 constexpr int PLANE_F0LO = 18;
 
+// Population storage.  FP32: 19 float planes (f_0 as the pair f_0 + f_0lo).  FP16 / BF16: the
+// rest population f_0 ~ phi stays one float plane (16-bit rounding of an O(1) value would
+// drift phi by ~1e-4 per step); the 17 other populations, all O(mu, u), are 16-bit planes
+// after it, stored as value x scale (a power of two keeping FP16 in its normal range).
+constexpr int ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2;
+
+__host__ __device__ constexpr long long state_bytes_per_cell(int st) { return st == ST_FP32 ? 4 * N_PLANES : 4 + 2 * 17; }
+
 struct Grid {
-  const float* src;     // post-collision state at t-1 (read)
-  float* dst;           // post-collision state at t (write)
+  const void* src;      // post-collision state at t-1 (read)
+  void* dst;            // post-collision state at t (write)
   int plane;            // elements per plane (ny * pitch); all planes fit in 2^31 elements
+  int storage;          // ST_FP32 / ST_FP16 / ST_BF16
+  float sf, isf;        // 16-bit scale of the f planes and its inverse
+  float sg, isg;        // 16-bit scale of the gbar planes and its inverse
   int nx, ny, pitch;
   int bc_x, bc_y;
   int tile_w;           // interior columns per strip
@@ -138,17 +151,43 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
+// Population a (0..8 f, 9..17 gbar, 18 f_0lo) at element idx of its plane.
+template <int ST>
+__device__ __forceinline__ float ld_pop(const void* __restrict__ base, int plane, int a, int idx, float inv_scale) {
+  if (ST == ST_FP32) return __ldg(static_cast<const float*>(base) + a * plane + idx);
+  if (a == 0) return __ldg(static_cast<const float*>(base) + idx);
+  const unsigned short* h = reinterpret_cast<const unsigned short*>(static_cast<const float*>(base) + plane);
+  const unsigned short raw = __ldg(h + (a - 1) * plane + idx);
+  const float v = ST == ST_FP16 ? __half2float(__ushort_as_half(raw)) : __bfloat162float(__ushort_as_bfloat16(raw));
+  return __fmul_rn(v, inv_scale);   // never contracted: identical rounding in every kernel
+}
+
+template <int ST>
+__device__ __forceinline__ void st_pop(void* __restrict__ base, int plane, int a, int idx, float v, float scale) {
+  if (ST == ST_FP32) {
+    static_cast<float*>(base)[a * plane + idx] = v;
+  } else if (a == 0) {
+    static_cast<float*>(base)[idx] = v;
+  } else {
+    unsigned short* h = reinterpret_cast<unsigned short*>(static_cast<float*>(base) + plane);
+    const float sv = __fmul_rn(v, scale);
+    h[(a - 1) * plane + idx] = ST == ST_FP16 ? __half_as_ushort(__float2half_rn(sv))
+                                             : __bfloat16_as_ushort(__float2bfloat16_rn(sv));
+  }
+}
+
 // Pull the 9 pre-collision populations of one distribution (planes starting at `src`):
 // v[a] = P*_a(x - e_a), or P*_opp(a)(x) when x - e_a lies beyond a wall (half-way bounce-back).
 // Cells with no wall neighbour take the branch-free path.
-__device__ __forceinline__ void gather9(const float* __restrict__ src, int plane, const ColNb& c, const RowNb& r,
-                                        float v[Q]) {
+template <int ST, int FIRST>
+__device__ __forceinline__ void gather9(const void* __restrict__ src, int plane, const ColNb& c, const RowNb& r,
+                                        float inv_scale, float v[Q]) {
   if (!(c.wl | c.wr | r.wb | r.wt)) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const int sx = cx(a) == 1 ? c.xm : (cx(a) == -1 ? c.xq : c.x0);
       const int sr = cy(a) == 1 ? r.rm : (cy(a) == -1 ? r.rq : r.r0);
-      v[a] = __ldg(src + a * plane + sr + sx);
+      v[a] = ld_pop<ST>(src, plane, FIRST + a, sr + sx, inv_scale);
     }
   } else {
 #pragma unroll
@@ -157,9 +196,8 @@ __device__ __forceinline__ void gather9(const float* __restrict__ src, int plane
       const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && r.wb) || (ey == -1 && r.wt);
       const int sx = ex == 1 ? c.xm : (ex == -1 ? c.xq : c.x0);
       const int sr = ey == 1 ? r.rm : (ey == -1 ? r.rq : r.r0);
-      const int i_pull = a * plane + sr + sx;
-      const int i_back = opp(a) * plane + r.r0 + c.x0;
-      v[a] = __ldg(src + (hit ? i_back : i_pull));
+      v[a] = hit ? ld_pop<ST>(src, plane, FIRST + opp(a), r.r0 + c.x0, inv_scale)
+                 : ld_pop<ST>(src, plane, FIRST + a, sr + sx, inv_scale);
     }
   }
 }
@@ -179,7 +217,8 @@ struct Rec {
 
 constexpr int RING = 8;      // rows of phi (hi, lo), mu and p, incl. one mirrored ghost row at a wall
 constexpr int RING_F = 6;    // f rows a-5..a awaiting S3 (thread-private)
-constexpr int NF = Q + 1;    // f_0..f_8 and f_0lo
+constexpr int NF = Q + 1;    // gathered f_0..f_8 and f_0lo
+constexpr int NFR = 8;       // f_1..f_8 kept for S3: f_0 is rebuilt there from the phi pair
 
 template <int NT>
 struct Smem {
@@ -187,7 +226,7 @@ struct Smem {
   float phi_lo[RING][NT];
   float mu[RING][NT];
   float p[RING][NT];
-  float2 f[RING_F][NT][NF / 2];  // own column only (no barrier needed); 64-bit accesses
+  float2 f[RING_F][NT][NFR / 2]; // own column only (no barrier needed); 64-bit accesses
   float g[2][Q][NT];             // own column only
 };
 
@@ -203,9 +242,9 @@ struct CollideC {
   float ux, uy, uu15, Fx, Fy, uF, Px, Py, uP, rho3, p, og, keep_g, src_g, of, keep_f, gmu, phi;
 };
 
-template <int A>
-__device__ __forceinline__ void collide_dir(const CollideC& k, const float f[NF], const float gb[Q], float* __restrict__ dst,
-                                            int plane, int cell, float& fsum, float& feqsum) {
+template <int ST, int A>
+__device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q], const float gb[Q], const Grid& g,
+                                            int cell, float& fsum, float& feqsum) {
   constexpr float w = wgt(A);
   const float eu = edot<A>(k.ux, k.uy);
   const float poly = A == 0 ? -k.uu15 : eu * (3.0f + 4.5f * eu) - k.uu15;
@@ -214,20 +253,21 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[NF]
   const float geq = w * k.p + k.rho3 * gmw;
   const float S = A == 0 ? (-k.uF) * gam + k.uP * gmw
                          : (edot<A>(k.Fx, k.Fy) - k.uF) * gam - (edot<A>(k.Px, k.Py) - k.uP) * gmw;
-  dst[(Q + A) * plane + cell] = k.keep_g * gb[A] + k.og * geq + k.src_g * S;
+  st_pop<ST>(g.dst, g.plane, Q + A, cell, k.keep_g * gb[A] + k.og * geq + k.src_g * S, g.sg);
   if (A > 0) {
     const float feq = w * (k.gmu + k.phi * poly);
     fsum += f[A];
     feqsum += feq;
-    dst[A * plane + cell] = k.keep_f * f[A] + k.of * feq;
+    st_pop<ST>(g.dst, g.plane, A, cell, k.keep_f * f[A] + k.of * feq, g.sf);
   }
 }
 
 // Collision of both distributions at one cell and store of the post-collision populations.
 // f[] holds f_0..f_8 and f_0lo (index Q), gb[] gbar_0..gbar_8.
-__device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx, float gpy,
-                                              const float f[NF], const float gb[Q], float* __restrict__ dst,
-                                              int plane, int cell) {
+template <int ST>
+__device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx, float gpy, float phi_hi,
+                                              float phi_lo, const float f[Q], const float gb[Q], const Grid& g,
+                                              int cell) {
   CollideC k;
   k.ux = r.ux;
   k.uy = r.uy;
@@ -248,20 +288,26 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   k.gmu = P.three_gamma_f * r.mu;
   k.phi = r.phi;
   float fsum = 0.0f, feqsum = 0.0f;
-  collide_dir<0>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<1>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<2>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<3>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<4>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<5>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<6>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<7>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  collide_dir<8>(k, f, gb, dst, plane, cell, fsum, feqsum);
-  // f_0^eq - f_0 = (phi - f_0) - sum_{a>0} f^eq_a = sum_{a>0} (f_a - f^eq_a): small, exact inputs
+  collide_dir<ST, 0>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 1>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 2>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 3>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 4>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 5>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 6>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 7>(k, f, gb, g, cell, fsum, feqsum);
+  collide_dir<ST, 8>(k, f, gb, g, cell, fsum, feqsum);
+  // f_0 = phi - sum_{a>0} f_a and f_0^eq - f_0 = sum_{a>0} (f_a - f^eq_a), so
+  // f*_0 = phi_hi + [(phi_lo - sum f_a) + omega_f (sum f_a - sum f^eq_a)]: only small terms are
+  // rounded before the one error-free sum with the O(1) high word.
   float hi, lo;
-  two_sum(f[0], f[Q] + P.omega_f * (fsum - feqsum), hi, lo);
-  dst[cell] = hi;
-  dst[PLANE_F0LO * plane + cell] = lo;
+  two_sum(phi_hi, (phi_lo - fsum) + P.omega_f * (fsum - feqsum), hi, lo);
+  if (ST == ST_FP32) {
+    st_pop<ST>(g.dst, g.plane, 0, cell, hi, 1.0f);
+    st_pop<ST>(g.dst, g.plane, PLANE_F0LO, cell, lo, 1.0f);
+  } else {
+    st_pop<ST>(g.dst, g.plane, 0, cell, hi + lo, 1.0f);
+  }
 }
 
 // The fused step (MODE_STEP) or the moment evaluation (MODE_MOMENTS) over one tile:
@@ -272,9 +318,11 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
 // thread that computes a value next to a wall also stores it into that ghost slot, so no read
 // is remapped.  Only one ghost row/column is ever read because every stage runs on real cells
 // and the stencils have radius 1.
-template <int NT, int MODE>
-__device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const MomentOut& mo, int strip, int seg,
-                                         Smem<NT>& sm) {
+// Not inlined: the single-simulation kernel and the batch kernel call one compiled body, so
+// their arithmetic (including every multiply-add contraction) is identical by construction.
+template <int NT, int MODE, int ST>
+__device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
+                                      Smem<NT>& sm) {
   const int t = threadIdx.x;
   const int x0 = strip * g.tile_w;
   const int x_end = min(x0 + g.tile_w, g.nx);
@@ -297,9 +345,6 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
   auto ghost_row = [&](int r) { return !ywall ? NOROW : (r == 0 ? -1 : (r == g.ny - 1 ? g.ny : NOROW)); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
   const ColNb cn = make_col(xp, g);
-  const float* __restrict__ srcF = g.src;
-  const float* __restrict__ srcG = g.src + Q * g.plane;
-  const float* __restrict__ srcL = g.src + PLANE_F0LO * g.plane;
 
   // stores one ring value plus its mirrored ghost copies
   auto put = [&](float (*ring)[NT], int r, float v) {
@@ -316,12 +361,12 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
   float fp[NF], gp[Q];
   auto fetch_f = [&](int r) {
     const RowNb rn = make_row(wrap1(r, g.ny), g);
-    gather9(srcF, g.plane, cn, rn, fp);
-    fp[Q] = __ldg(srcL + rn.r0 + cn.x0);
+    gather9<ST, 0>(g.src, g.plane, cn, rn, g.isf, fp);
+    fp[Q] = ST == ST_FP32 ? ld_pop<ST>(g.src, g.plane, PLANE_F0LO, rn.r0 + cn.x0, 1.0f) : 0.0f;
   };
   auto fetch_g = [&](int r) {
     const RowNb rn = make_row(wrap1(r, g.ny), g);
-    gather9(srcG, g.plane, cn, rn, gp);
+    gather9<ST, Q>(g.src, g.plane, cn, rn, g.isg, gp);
   };
   auto s0_active = [&](int r) { return r <= yb + 2 && in_w3 && row_ok(r); };
   auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
@@ -339,7 +384,7 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
       put(sm.phi_lo, a, lo);
       if (MODE == MODE_STEP && in_w0 && a >= ya) {
 #pragma unroll
-        for (int k = 0; k < NF / 2; ++k) sm.f[fslot][t][k] = make_float2(fp[2 * k], fp[2 * k + 1]);
+        for (int k = 0; k < NFR / 2; ++k) sm.f[fslot][t][k] = make_float2(fp[2 * k + 1], fp[2 * k + 2]);
       }
     }
     if (s0_active(a + 1)) fetch_f(a + 1);
@@ -449,16 +494,18 @@ __device__ __forceinline__ void run_tile(const Phys& P, const Grid& g, const Mom
         const float gpy = (4.0f * (qn[t] - qs[t]) + ((qn[t + 1] - qs[t + 1]) + (qn[t - 1] - qs[t - 1]))) *
                           (1.0f / 12.0f);
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
-        float f[NF], gb[Q];
+        float f[Q], gb[Q];
+        f[0] = 0.0f;   // unused: f_0 follows from the phi pair
 #pragma unroll
-        for (int k = 0; k < NF / 2; ++k) {
+        for (int k = 0; k < NFR / 2; ++k) {
           const float2 v = sm.f[rslot][t][k];
-          f[2 * k] = v.x;
-          f[2 * k + 1] = v.y;
+          f[2 * k + 1] = v.x;
+          f[2 * k + 2] = v.y;
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
-        collide_store(P, prev, q0[t], gpx, gpy, f, gb, g.dst, g.plane, r * g.pitch + xp);
+        collide_store<ST>(P, prev, q0[t], gpx, gpy, sm.phi_hi[r & (RING - 1)][t], sm.phi_lo[r & (RING - 1)][t], f, gb,
+                          g, r * g.pitch + xp);
       }
     }
     prev = cur;

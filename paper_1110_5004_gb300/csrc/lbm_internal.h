@@ -13,7 +13,7 @@ struct lbm_sim {
   lbm_params params{};
   lbm::Phys phys{};
   cudaStream_t stream = nullptr;
-  float* buf[2] = {nullptr, nullptr};  // N_PLANES planes each (post-collision state)
+  void* buf[2] = {nullptr, nullptr};   // post-collision state, state_bytes_per_cell x plane each
   int cur = 0;                         // buffer holding the current state
   float* fields = nullptr;             // 6 planes: phi, rho, ux, uy, p, mu (moments and init)
   double* red = nullptr;               // reduction scratch: ny rows x 12 partials + final record
@@ -24,6 +24,7 @@ struct lbm_sim {
   int seg_h = 0;                       // rows per CTA (0: chosen to fill the GPU)
   int sms = 0;                         // multiprocessors of the device
   int occ = 0;                         // resident step CTAs per SM at the current nt
+  float sf = 1.0f, sg = 1.0f;          // 16-bit storage scales of the f and gbar planes
   lbm_batch* batch = nullptr;
 };
 
@@ -35,7 +36,7 @@ constexpr int DIAG_PARTIALS = 12;
 void set_error(const char* fmt, ...);
 int cuda_fail(cudaError_t e, const char* what);
 Phys make_phys(const lbm_params& p);
-Grid make_grid(const lbm_sim* s, const float* src, float* dst);
+Grid make_grid(const lbm_sim* s, const void* src, void* dst);
 // Strip width, strip count and segment height for an nx x ny grid: strips of at most nt - 6
 // columns with balanced widths; seg_h = 0 picks the height that puts about one full wave of
 // CTAs (slots = SMs x CTAs per SM) on the device.

@@ -8,36 +8,46 @@ namespace lbm {
 
 // ------------------------------------------------------------------ fused step / moments
 
-template <int NT, int MODE>
+template <int NT, int MODE, int ST>
 __global__ void __launch_bounds__(NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
   const int strip = blockIdx.x % g.n_strips;
   const int seg = blockIdx.x / g.n_strips;
-  run_tile<NT, MODE>(P, g, mo, strip, seg, sm);
+  run_tile<NT, MODE, ST>(P, g, mo, strip, seg, sm);
 }
 
 static int n_tiles(const Grid& g) { return g.n_strips * ((g.ny + g.seg_h - 1) / g.seg_h); }
 
-template <int NT, int MODE>
+template <int NT, int MODE, int ST>
 static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
   static bool attr_set = false;   // one GPU per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(Smem<NT>));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_tiles<NT, MODE><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
+  k_tiles<NT, MODE, ST><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
   return cudaGetLastError();
+}
+
+template <int MODE, int ST>
+static cudaError_t launch_st(const Phys& P, const Grid& g, const MomentOut& mo, int nt, cudaStream_t st) {
+  switch (nt) {
+    case 64: return launch_nt<64, MODE, ST>(P, g, mo, st);
+    case 128: return launch_nt<128, MODE, ST>(P, g, mo, st);
+    case 256: return launch_nt<256, MODE, ST>(P, g, mo, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 template <int MODE>
 static cudaError_t launch_tiles(const Phys& P, const Grid& g, const MomentOut& mo, int nt, cudaStream_t st) {
-  switch (nt) {
-    case 64: return launch_nt<64, MODE>(P, g, mo, st);
-    case 128: return launch_nt<128, MODE>(P, g, mo, st);
-    case 256: return launch_nt<256, MODE>(P, g, mo, st);
+  switch (g.storage) {
+    case ST_FP32: return launch_st<MODE, ST_FP32>(P, g, mo, nt, st);
+    case ST_FP16: return launch_st<MODE, ST_FP16>(P, g, mo, nt, st);
+    case ST_BF16: return launch_st<MODE, ST_BF16>(P, g, mo, nt, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -46,8 +56,9 @@ template <int NT>
 static int occupancy_nt() {
   int occ = 0;
   // the dynamic shared-memory size above 48 KB is only admitted once the attribute is set
-  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<NT>));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP>, NT, sizeof(Smem<NT>));
+  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP, ST_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(Smem<NT>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP, ST_FP32>, NT, sizeof(Smem<NT>));
   cudaGetLastError();
   return occ > 0 ? occ : 1;
 }
@@ -92,6 +103,7 @@ __global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
 // Post-collision-layout state whose pull gives f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0):
 // plane a at cell z holds the equilibrium of direction a at z + e_a, or, when that link leaves
 // through a wall, the equilibrium of the reversed direction at z itself.
+template <int ST>
 __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int y = blockIdx.y;
@@ -137,12 +149,16 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
       }
       float hi, lo;
       two_sum(ph, -rest, hi, lo);
-      g.dst[cell] = hi;
-      g.dst[(long long)PLANE_F0LO * g.plane + cell] = lo;
+      if (ST == ST_FP32) {
+        st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi, 1.0f);
+        st_pop<ST>(g.dst, g.plane, PLANE_F0LO, (int)cell, lo, 1.0f);
+      } else {
+        st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi + lo, 1.0f);
+      }
     } else {
-      g.dst[(long long)a * g.plane + cell] = w * (P.three_gamma_f * m + ph * poly);
+      st_pop<ST>(g.dst, g.plane, a, (int)cell, w * (P.three_gamma_f * m + ph * poly), g.sf);
     }
-    g.dst[(long long)(Q + a) * g.plane + cell] = geq;
+    st_pop<ST>(g.dst, g.plane, Q + a, (int)cell, geq, g.sg);
   }
 }
 
@@ -152,7 +168,11 @@ cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
   k_init_mu<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_init_pop<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
+  switch (g.storage) {
+    case ST_FP16: k_init_pop<ST_FP16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
+    case ST_BF16: k_init_pop<ST_BF16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
+    default: k_init_pop<ST_FP32><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
+  }
   return cudaGetLastError();
 }
 

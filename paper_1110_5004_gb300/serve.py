@@ -1,0 +1,215 @@
+"""Continuous-batching server for simulation requests.
+
+Requests (a workload and a step count) arrive over time.  Admitted requests keep their f/g
+state resident on the device as members of one ragged batch; each round advances every member
+by one chunk of steps in a single CUDA-graph replay (one persistent launch per step over the
+tiles of all members).  Between rounds the server
+  - retires members that reached their step count (FP64 diagnostics and, optionally, the
+    moment fields copied back to the host; the member's device memory is freed),
+  - retires members whose state stopped being finite (failure detection, LBM_ERR_DIVERGED),
+  - admits waiting requests, first come first served, while the device-memory budget, the
+    member cap and the cap on lattice cells in flight allow (a request larger than the whole
+    budget is rejected at once; the cell cap never blocks the only request).
+Latency is measured from arrival to the result being on the host.  `run_plain` serves the same
+stream back to back, one plain simulation at a time, as the baseline.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from typing import Dict, List, Optional
+
+import numpy as np
+
+from . import LBM_FP32, Batch, Sim, device_bytes
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    workload: object          # workloads.Workload
+    steps: int
+    arrival_s: float = 0.0
+    storage: int = LBM_FP32
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    status: str               # "done" | "diverged" | "rejected" | "cancelled"
+    steps_done: int
+    arrival_s: float
+    admit_s: Optional[float]
+    finish_s: float
+    diagnostics: Optional[dict] = None
+    fields: Optional[Dict[str, np.ndarray]] = None
+
+    @property
+    def latency_s(self):
+        return self.finish_s - self.arrival_s
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else float("nan")
+
+
+def summarize(results: List[Result], wall_s: float) -> dict:
+    done = [r for r in results if r.status == "done"]
+    lat = [r.latency_s for r in results if r.status in ("done", "diverged")]
+    lu = sum(r.steps_done * r.diagnostics_cells for r in results if hasattr(r, "diagnostics_cells"))
+    return {"requests": len(results), "done": len(done),
+            "diverged": sum(r.status == "diverged" for r in results),
+            "rejected": sum(r.status == "rejected" for r in results),
+            "p50_s": percentile(lat, 50), "p99_s": percentile(lat, 99), "wall_s": wall_s,
+            "lattice_updates": lu, "mlups": lu / wall_s / 1e6 if wall_s > 0 else float("nan")}
+
+
+class _Member:
+    def __init__(self, req: Request, sim: Sim, slot: int, admit_s: float, check_steps: int):
+        self.req, self.sim, self.slot, self.admit_s = req, sim, slot, admit_s
+        self.remaining = req.steps
+        self.next_check = check_steps
+
+
+class Server:
+    def __init__(self, budget_bytes: int, max_members: int = 256, chunk_steps: int = 200,
+                 check_steps: int = 200, keep_fields: bool = False, stream=None, tile=None,
+                 max_cells: int = 4 << 20):
+        import torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.budget = int(budget_bytes)
+        self.batch = Batch(budget_bytes=self.budget, stream=self.stream)
+        if tile is not None:
+            self.batch.set_tile(*tile)
+        self.max_members = max_members
+        # lattice cells in flight that already fill the device: admitting beyond them only
+        # stretches every member's latency (processor sharing) without adding throughput
+        self.max_cells = max_cells
+        self.chunk = chunk_steps
+        self.check_steps = check_steps     # a member is checked for divergence every this many steps
+        self.keep_fields = keep_fields
+        self.cancelled = set()
+        self.max_concurrent = 0
+        self.rounds = 0
+
+    def cancel(self, rid: int):
+        self.cancelled.add(rid)
+
+    def _finish(self, m: _Member, status: str, now: float, results: List[Result]):
+        diag = m.sim.diagnostics()
+        fields = m.sim.moments() if self.keep_fields and status == "done" else None
+        self.batch.remove(m.slot)
+        m.sim.close()
+        r = Result(m.req.rid, status, m.req.steps - m.remaining, m.req.arrival_s, m.admit_s, now(), diag, fields)
+        r.diagnostics_cells = m.req.workload.cells
+        results.append(r)
+
+    def run(self, requests: List[Request], realtime: bool = True) -> List[Result]:
+        """Serve `requests` (arrival times in seconds from the start).  With realtime=False the
+        arrival clock jumps to the next arrival whenever the device would otherwise idle."""
+        pending = sorted(requests, key=lambda r: r.arrival_s)
+        waiting: List[Request] = []
+        active: Dict[int, _Member] = {}
+        results: List[Result] = []
+        t0 = time.perf_counter()
+        offset = [0.0]
+
+        def now():
+            return time.perf_counter() - t0 + offset[0]
+
+        while pending or waiting or active:
+            t = now()
+            while pending and pending[0].arrival_s <= t:
+                waiting.append(pending.pop(0))
+            # cancellations
+            for r in [r for r in waiting if r.rid in self.cancelled]:
+                waiting.remove(r)
+                results.append(Result(r.rid, "cancelled", 0, r.arrival_s, None, now()))
+            for m in [m for m in active.values() if m.req.rid in self.cancelled]:
+                del active[m.slot]
+                self._finish(m, "cancelled", now, results)
+            # admission, first come first served
+            while waiting:
+                r = waiting[0]
+                need = device_bytes(r.workload.nx, r.workload.ny, r.storage)
+                if need > self.budget:
+                    waiting.pop(0)
+                    results.append(Result(r.rid, "rejected", 0, r.arrival_s, None, now()))
+                    continue
+                cells = sum(m.req.workload.cells for m in active.values())
+                if self.batch.bytes + need > self.budget or len(active) >= self.max_members or \
+                        (active and cells + r.workload.cells > self.max_cells):
+                    break
+                sim = Sim.from_workload(r.workload, storage=r.storage, stream=self.stream)
+                slot = self.batch.try_add(sim)
+                if slot is None:            # the library's own budget check agrees with ours
+                    sim.close()
+                    break
+                waiting.pop(0)
+                active[slot] = _Member(r, sim, slot, now(), self.check_steps)
+            self.max_concurrent = max(self.max_concurrent, len(active))
+            if not active:
+                if pending:
+                    wait = pending[0].arrival_s - now()
+                    if wait > 0:
+                        if realtime:
+                            time.sleep(min(wait, 0.05))
+                        else:
+                            offset[0] += wait
+                continue
+            # rounds end where a member finishes or is due for its divergence check
+            k = min(self.chunk, min(min(m.remaining, m.next_check - (m.req.steps - m.remaining))
+                                    for m in active.values()))
+            self.batch.step(k)
+            self.rounds += 1
+            for m in active.values():
+                m.remaining -= k
+            finished = [m for m in active.values() if m.remaining == 0]
+            for m in finished:
+                del active[m.slot]
+                self._finish(m, "done", now, results)
+            for m in list(active.values()):
+                done = m.req.steps - m.remaining
+                if done >= m.next_check:
+                    m.next_check += self.check_steps
+                    if not m.sim.diagnostics()["finite"]:
+                        del active[m.slot]
+                        self._finish(m, "diverged", now, results)
+        return sorted(results, key=lambda r: r.rid)
+
+    def close(self):
+        self.batch.close()
+
+
+def run_plain(requests: List[Request], keep_fields: bool = False, stream=None, realtime: bool = True,
+              check_every_steps: int = 200) -> List[Result]:
+    """Back-to-back baseline: one plain simulation at a time, in arrival order."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    results = []
+    t0 = time.perf_counter()
+    offset = 0.0
+    for r in sorted(requests, key=lambda r: r.arrival_s):
+        t = time.perf_counter() - t0 + offset
+        if r.arrival_s > t:
+            if realtime:
+                time.sleep(r.arrival_s - t)
+            else:
+                offset += r.arrival_s - t
+        start = time.perf_counter() - t0 + offset
+        sim = Sim.from_workload(r.workload, storage=r.storage, stream=stream)
+        done, status = 0, "done"
+        while done < r.steps:
+            n = min(check_every_steps, r.steps - done)
+            sim.step(n)
+            done += n
+            if done < r.steps and not sim.diagnostics()["finite"]:
+                status = "diverged"
+                break
+        diag = sim.diagnostics()
+        fields = sim.moments() if keep_fields and status == "done" else None
+        sim.close()
+        res = Result(r.rid, status, done, r.arrival_s, start, time.perf_counter() - t0 + offset, diag, fields)
+        res.diagnostics_cells = r.workload.cells
+        results.append(res)
+    return sorted(results, key=lambda r: r.rid)
