@@ -152,6 +152,19 @@ class ClockSampler:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+def replica_throughput(local_seconds, updates_per_rank, world, device=None):
+    """Whole-job throughput of N independent replicas: every rank did the same work, the job
+    took as long as the slowest rank (max over ranks), value = all ranks' updates / that time."""
+    import torch
+    import torch.distributed as dist
+    slowest = float(local_seconds)
+    if world > 1:
+        t = torch.tensor([slowest], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        slowest = float(t.item())
+    return world * updates_per_rank / slowest / 1e6, slowest
+
+
 def cpu_baseline(w, steps):
     """The FP64 oracle, as it stands, on the host cores: `steps` steps of the workload with the
     same re-initialisation cadence."""
@@ -323,12 +336,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     launches = sim.launch_count - launches0 - 2 * ((args.steps + REINIT_EVERY - 1) // REINIT_EVERY)
     per_step = [a.elapsed_time(b) * 1e-3 for a, b in zip(ev0, ev1)]
-    total = sum(per_step)
-    if world > 1:
-        t = torch.tensor([total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
-    value = world * w.cells * args.steps / total / 1e6
+    value, total = replica_throughput(sum(per_step), w.cells * args.steps, world, device="cuda")
     mean_step = sum(per_step) / len(per_step)
     peak, peak_kind = measured_peaks()
     achieved = B_MIN_FP32 * w.cells / mean_step / 1e9
@@ -361,12 +369,8 @@ def run_ours(args):
         for _ in range(args.e2e_iters):
             e2e_iter()
         torch.cuda.synchronize()
-        e2e_t = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_t = float(t.item())
-        e2e_value = world * w.cells * REINIT_EVERY * args.e2e_iters / e2e_t / 1e6
+        e2e_value, _ = replica_throughput(time.perf_counter() - t0, w.cells * REINIT_EVERY * args.e2e_iters,
+                                          world, device="cuda")
         assert np.isfinite(h_out_np["phi"]).all(), "non-finite state inside the re-initialisation window"
 
     cpu = None

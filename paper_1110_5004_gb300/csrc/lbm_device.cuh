@@ -220,14 +220,14 @@ constexpr int RING_F = 6;    // f rows a-5..a awaiting S3 (thread-private)
 constexpr int NF = Q + 1;    // gathered f_0..f_8 and f_0lo
 constexpr int NFR = 8;       // f_1..f_8 kept for S3: f_0 is rebuilt there from the phi pair
 
+// Row ring fields, interleaved per slot so that one slot offset serves every field.
+enum { R_PHI_HI = 0, R_PHI_LO = 1, R_MU = 2, R_P = 3, R_FIELDS = 4 };
+
 template <int NT>
 struct Smem {
-  float phi_hi[RING][NT];
-  float phi_lo[RING][NT];
-  float mu[RING][NT];
-  float p[RING][NT];
-  float2 f[RING_F][NT][NFR / 2]; // own column only (no barrier needed); 64-bit accesses
-  float g[2][Q][NT];             // own column only
+  float rows[RING][R_FIELDS][NT];  // phi (hi, lo), mu, p of recent rows
+  float2 f[RING_F][NT][NFR / 2];   // own column only (no barrier needed); 64-bit accesses
+  float g[2][Q][NT];               // own column only
 };
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
@@ -340,20 +340,29 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
   const bool in_w0 = t >= 3 && t < width + 3;
   // ghost column this thread also fills (its mirror image beyond a wall), or -1
   const int tg = (xwall && xl == 0) ? t - 1 : ((xwall && xl == g.nx - 1) ? t + 1 : -1);
-  // ghost row filled together with real row r, or a value no row takes
-  constexpr int NOROW = -1000000;
-  auto ghost_row = [&](int r) { return !ywall ? NOROW : (r == 0 ? -1 : (r == g.ny - 1 ? g.ny : NOROW)); };
+  const bool has_tg = tg >= 0;
+  constexpr int SLOT = R_FIELDS * NT;        // floats per ring slot
+  constexpr int RMASK = RING * SLOT - 1;     // ring size is a power of two
+  float* const ring = &sm.rows[0][0][0];
+  // slot offset (in floats) of row r; rows are consecutive integers, so offsets wrap
+  auto slot = [&](int r) { return (r * SLOT) & RMASK; };
+  // ghost row beyond a wall filled together with real row r (its mirror), as a slot offset
+  auto ghost_slot = [&](int r) { return r == 0 ? slot(-1) : slot(g.ny); };
+  auto is_wall_row = [&](int r) { return ywall && (r == 0 || r == g.ny - 1); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
   const ColNb cn = make_col(xp, g);
 
-  // stores one ring value plus its mirrored ghost copies
-  auto put = [&](float (*ring)[NT], int r, float v) {
-    ring[r & (RING - 1)][t] = v;
-    if (tg >= 0) ring[r & (RING - 1)][tg] = v;
-    const int gr = ghost_row(r);
-    if (gr != NOROW) {
-      ring[gr & (RING - 1)][t] = v;
-      if (tg >= 0) ring[gr & (RING - 1)][tg] = v;
+  // store field F of row r (slot offset so) plus its mirrored ghost copies
+  auto put = [&](int so, int r, int F, float v) {
+    ring[so + F * NT + t] = v;
+    const bool wrow = is_wall_row(r);
+    if (has_tg | wrow) {
+      if (has_tg) ring[so + F * NT + tg] = v;
+      if (wrow) {
+        const int gs = ghost_slot(r);
+        ring[gs + F * NT + t] = v;
+        if (has_tg) ring[gs + F * NT + tg] = v;
+      }
     }
   };
 
@@ -375,61 +384,61 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
   Rec cur{}, prev{};
   int fslot = 0;                             // (a - ya + 3) mod RING_F: ring slot of row a
   for (int a = ya - 3; a <= yb + 4; ++a) {
+    // slot offsets of the rows this iteration touches (a-7 .. a)
+    const int o0 = slot(a), o1 = slot(a - 1), o2 = slot(a - 2), o3 = slot(a - 3);
+    const int o4 = slot(a - 4), o5 = slot(a - 5), o6 = slot(a - 6);
     // ---- S0: phi at row a (as an unevaluated pair hi + lo)
     if (s0_active(a)) {
       const float small = fp[Q] + (((fp[1] + fp[2]) + (fp[3] + fp[4])) + ((fp[5] + fp[6]) + (fp[7] + fp[8])));
       float hi, lo;
       two_sum(fp[0], small, hi, lo);
-      put(sm.phi_hi, a, hi);
-      put(sm.phi_lo, a, lo);
+      put(o0, a, R_PHI_HI, hi);
+      put(o0, a, R_PHI_LO, lo);
       if (MODE == MODE_STEP && in_w0 && a >= ya) {
 #pragma unroll
         for (int k = 0; k < NFR / 2; ++k) sm.f[fslot][t][k] = make_float2(fp[2 * k + 1], fp[2 * k + 2]);
       }
     }
     if (s0_active(a + 1)) fetch_f(a + 1);
-    // ---- S1: mu at row a-2
+    // ---- S1: mu at row a-2 (rows a-3 .. a-1 of phi)
     {
       const int r = a - 2;
       if (r >= ya - 2 && r <= yb + 1 && in_w2 && row_ok(r)) {
-        const float* hs = sm.phi_hi[(r - 1) & (RING - 1)];
-        const float* h0 = sm.phi_hi[r & (RING - 1)];
-        const float* hn = sm.phi_hi[(r + 1) & (RING - 1)];
-        const float* ls = sm.phi_lo[(r - 1) & (RING - 1)];
-        const float* l0 = sm.phi_lo[r & (RING - 1)];
-        const float* ln = sm.phi_lo[(r + 1) & (RING - 1)];
-        const float H = h0[t], L = l0[t];
-        // differences from the centre: exact for neighbouring values of like magnitude
-        auto d = [&](const float* hr, const float* lr, int c) { return (hr[c] - H) + (lr[c] - L); };
-        const float lap = (4.0f * ((d(h0, l0, t + 1) + d(hn, ln, t)) + (d(h0, l0, t - 1) + d(hs, ls, t))) +
-                           ((d(hn, ln, t + 1) + d(hn, ln, t - 1)) + (d(hs, ls, t - 1) + d(hs, ls, t + 1)))) *
-                          (1.0f / 6.0f);
+        const float* hs = ring + o3 + R_PHI_HI * NT + t;
+        const float* h0 = ring + o2 + R_PHI_HI * NT + t;
+        const float* hn = ring + o1 + R_PHI_HI * NT + t;
+        const float* ls = ring + o3 + R_PHI_LO * NT + t;
+        const float* l0 = ring + o2 + R_PHI_LO * NT + t;
+        const float* ln = ring + o1 + R_PHI_LO * NT + t;
+        const float H = h0[0], L = l0[0];
+        // differences from the centre: exact for neighbouring values of like magnitude; the low
+        // words are tiny and are summed directly
+        const float dax = (h0[1] - H) + (hn[0] - H) + ((h0[-1] - H) + (hs[0] - H));
+        const float ddg = ((hn[1] - H) + (hn[-1] - H)) + ((hs[-1] - H) + (hs[1] - H));
+        const float lax = (l0[1] + ln[0]) + (l0[-1] + ls[0]);
+        const float ldg = (ln[1] + ln[-1]) + (ls[-1] + ls[1]);
+        const float lap = (4.0f * (dax + lax) + (ddg + ldg) - 20.0f * L) * (1.0f / 6.0f);
         const float ph = H + L;
         const float dm = (H - P.phi_star) + L, dp = (H + P.phi_star) + L;
-        put(sm.mu, r, P.four_beta * ph * dm * dp - P.kappa * lap);
+        put(o2, r, R_MU, P.four_beta * ph * dm * dp - P.kappa * lap);
       }
     }
-    // ---- S2: u, p at row a-4
+    // ---- S2: u, p at row a-4 (rows a-5 .. a-3 of phi and mu)
     {
       const int r = a - 4;
       if (s2_active(r)) {
-        const float* hs = sm.phi_hi[(r - 1) & (RING - 1)];
-        const float* h0 = sm.phi_hi[r & (RING - 1)];
-        const float* hn = sm.phi_hi[(r + 1) & (RING - 1)];
-        const float* l0 = sm.phi_lo[r & (RING - 1)];
-        const float* ms = sm.mu[(r - 1) & (RING - 1)];
-        const float* m0 = sm.mu[r & (RING - 1)];
-        const float* mn = sm.mu[(r + 1) & (RING - 1)];
+        const float* hs = ring + o5 + R_PHI_HI * NT + t;
+        const float* h0 = ring + o4 + R_PHI_HI * NT + t;
+        const float* hn = ring + o3 + R_PHI_HI * NT + t;
+        const float* ms = ring + o5 + R_MU * NT + t;
+        const float* m0 = ring + o4 + R_MU * NT + t;
+        const float* mn = ring + o3 + R_MU * NT + t;
         // grad phi only feeds grad rho (density and pressure terms): the high words suffice
-        const float ph = h0[t] + l0[t];
-        const float gphx = (4.0f * (h0[t + 1] - h0[t - 1]) + ((hn[t + 1] - hn[t - 1]) + (hs[t + 1] - hs[t - 1]))) *
-                           (1.0f / 12.0f);
-        const float gphy = (4.0f * (hn[t] - hs[t]) + ((hn[t + 1] - hs[t + 1]) + (hn[t - 1] - hs[t - 1]))) *
-                           (1.0f / 12.0f);
-        const float gmx = (4.0f * (m0[t + 1] - m0[t - 1]) + ((mn[t + 1] - mn[t - 1]) + (ms[t + 1] - ms[t - 1]))) *
-                          (1.0f / 12.0f);
-        const float gmy = (4.0f * (mn[t] - ms[t]) + ((mn[t + 1] - ms[t + 1]) + (mn[t - 1] - ms[t - 1]))) *
-                          (1.0f / 12.0f);
+        const float ph = h0[0] + ring[o4 + R_PHI_LO * NT + t];
+        const float gphx = (4.0f * (h0[1] - h0[-1]) + ((hn[1] - hn[-1]) + (hs[1] - hs[-1]))) * (1.0f / 12.0f);
+        const float gphy = (4.0f * (hn[0] - hs[0]) + ((hn[1] - hs[1]) + (hn[-1] - hs[-1]))) * (1.0f / 12.0f);
+        const float gmx = (4.0f * (m0[1] - m0[-1]) + ((mn[1] - mn[-1]) + (ms[1] - ms[-1]))) * (1.0f / 12.0f);
+        const float gmy = (4.0f * (mn[0] - ms[0]) + ((mn[1] - ms[1]) + (mn[-1] - ms[-1]))) * (1.0f / 12.0f);
         const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
         const float rho = P.rho_B + cl * P.drho;
         const float fsx = -ph * gmx;
@@ -437,8 +446,8 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float gy = -rho * P.gravity;
         float sdef = 0.0f;
         if (P.remove_Fa) {
-          const float lmu = (4.0f * (m0[t + 1] + mn[t] + m0[t - 1] + ms[t]) + (mn[t + 1] + mn[t - 1] + ms[t - 1] + ms[t + 1]) -
-                             20.0f * m0[t]) * (1.0f / 6.0f);
+          const float lmu = (4.0f * (m0[1] + mn[0] + m0[-1] + ms[0]) + (mn[1] + mn[-1] + ms[-1] + ms[1]) -
+                             20.0f * m0[0]) * (1.0f / 6.0f);
           sdef = P.s_coef * lmu;
         }
         const float* gb = gp;
@@ -451,7 +460,7 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float uy = (3.0f * jy + 0.5f * (fsy + gy)) * rden;
         const float drx = P.rho_prime * gphx, dry = P.rho_prime * gphy;
         const float p = m0g + (1.0f / 6.0f) * (ux * drx + uy * dry);
-        put(sm.p, r, p);
+        put(o4, r, R_P, p);
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && r >= ya && r < yb) {
             const int o = r * g.pitch + xp;
@@ -467,7 +476,7 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
             for (int k = 0; k < Q; ++k) sm.g[r & 1][k][t] = gb[k];
           }
           cur.phi = ph;
-          cur.mu = m0[t];
+          cur.mu = m0[0];
           cur.rho = rho;
           cur.ux = ux;
           cur.uy = uy;
@@ -482,17 +491,15 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
       if (s2_active(r + 1)) fetch_g(r + 1);
     }
     __syncthreads();
-    // ---- S3: collide and store row a-5
+    // ---- S3: collide and store row a-5 (p of rows a-6 .. a-4)
     if (MODE == MODE_STEP) {
       const int r = a - 5;
       if (r >= ya && r < yb && in_w0) {
-        const float* qs = sm.p[(r - 1) & (RING - 1)];
-        const float* q0 = sm.p[r & (RING - 1)];
-        const float* qn = sm.p[(r + 1) & (RING - 1)];
-        const float gpx = (4.0f * (q0[t + 1] - q0[t - 1]) + ((qn[t + 1] - qn[t - 1]) + (qs[t + 1] - qs[t - 1]))) *
-                          (1.0f / 12.0f);
-        const float gpy = (4.0f * (qn[t] - qs[t]) + ((qn[t + 1] - qs[t + 1]) + (qn[t - 1] - qs[t - 1]))) *
-                          (1.0f / 12.0f);
+        const float* qs = ring + o6 + R_P * NT + t;
+        const float* q0 = ring + o5 + R_P * NT + t;
+        const float* qn = ring + o4 + R_P * NT + t;
+        const float gpx = (4.0f * (q0[1] - q0[-1]) + ((qn[1] - qn[-1]) + (qs[1] - qs[-1]))) * (1.0f / 12.0f);
+        const float gpy = (4.0f * (qn[0] - qs[0]) + ((qn[1] - qs[1]) + (qn[-1] - qs[-1]))) * (1.0f / 12.0f);
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
         float f[Q], gb[Q];
         f[0] = 0.0f;   // unused: f_0 follows from the phi pair
@@ -504,8 +511,8 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
-        collide_store<ST>(P, prev, q0[t], gpx, gpy, sm.phi_hi[r & (RING - 1)][t], sm.phi_lo[r & (RING - 1)][t], f, gb,
-                          g, r * g.pitch + xp);
+        collide_store<ST>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], f,
+                          gb, g, r * g.pitch + xp);
       }
     }
     prev = cur;
