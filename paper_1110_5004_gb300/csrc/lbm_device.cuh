@@ -338,8 +338,9 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
   const bool in_w2 = t >= 1 && t < width + 5 && col_real;
   const bool in_w1 = t >= 2 && t < width + 4 && col_real;
   const bool in_w0 = t >= 3 && t < width + 3;
-  // ghost column this thread also fills (its mirror image beyond a wall), or -1
-  const int tg = (xwall && xl == 0) ? t - 1 : ((xwall && xl == g.nx - 1) ? t + 1 : -1);
+  // ghost column this thread also fills (its mirror image beyond a wall), or -1; a ghost that
+  // falls outside the ring (the strip ends 3 columns short of the right wall) is never read
+  const int tg = (xwall && xl == 0) ? t - 1 : ((xwall && xl == g.nx - 1 && t + 1 < NT) ? t + 1 : -1);
   const bool has_tg = tg >= 0;
   constexpr int SLOT = R_FIELDS * NT;        // floats per ring slot
   constexpr int RMASK = RING * SLOT - 1;     // ring size is a power of two

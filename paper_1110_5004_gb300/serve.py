@@ -90,6 +90,7 @@ class Server:
         self.keep_fields = keep_fields
         self.cancelled = set()
         self.max_concurrent = 0
+        self.max_bytes = 0                 # peak device bytes held by members
         self.rounds = 0
 
     def cancel(self, rid: int):
@@ -148,6 +149,7 @@ class Server:
                 waiting.pop(0)
                 active[slot] = _Member(r, sim, slot, now(), self.check_steps)
             self.max_concurrent = max(self.max_concurrent, len(active))
+            self.max_bytes = max(self.max_bytes, self.batch.bytes)
             if not active:
                 if pending:
                     wait = pending[0].arrival_s - now()

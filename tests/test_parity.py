@@ -86,9 +86,10 @@ def test_many_tiles_and_ragged_tails(lbm, tile):
     assert_parity(got, ref, w)
 
 
-def test_tile_shape_does_not_change_results(lbm):
+@pytest.mark.parametrize("nx", [150, 151])
+def test_tile_shape_does_not_change_results(lbm, nx):
     """Per-cell arithmetic is independent of the tile shape: bitwise-identical states."""
-    w = W.random_small(150, 44, seed=21, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    w = W.random_small(nx, 44, seed=21, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
     outs = []
     for tile in ((64, 5), (128, 16), (256, 64), (128, 44)):
         s = lbm.Sim.from_workload(w, tile=tile)
@@ -97,6 +98,16 @@ def test_tile_shape_does_not_change_results(lbm):
     for o in outs[1:]:
         for k in o:
             assert np.array_equal(o[k], outs[0][k]), k
+
+
+@pytest.mark.parametrize("nx,tile", [(3193, (64, 0)), (14521, (128, 0)), (131, (64, 9)), (250, (64, 9))])
+def test_strip_ending_short_of_a_side_wall(lbm, nx, tile):
+    """Side walls with many strips, among them the widths whose second-to-last strip ends 3
+    columns before the right wall (64 threads: 58-column strips; 128 threads: 122-column
+    strips), so the wall's ghost column falls just outside that strip's ring."""
+    w = W.random_small(nx, 6, seed=30 + nx % 7, bc_x=W.WALL, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    _, got, ref = run_both(lbm, w, 20, tile=tile)
+    assert_parity(got, ref, w)
 
 
 @pytest.mark.parametrize("rf", [0, 1])

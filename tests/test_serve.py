@@ -85,6 +85,7 @@ def test_admission_respects_budget_and_order(fake_server):
     assert all(r.steps_done == q.steps for r, q in zip(res, reqs))
     assert srv.max_concurrent == 2
     assert max(n for _, n in srv.batch.history) == 2
+    assert srv.max_bytes == 200
     # first come first served: admission times are non-decreasing in arrival order
     admits = [r.admit_s for r in res]
     assert admits == sorted(admits)
@@ -179,7 +180,7 @@ def test_served_budget_failure_and_cancel(lbm):
     assert res[99].status == "rejected"
     assert res[2].status == "diverged"
     assert res[4].status == "cancelled"
-    assert srv.max_concurrent <= 2
+    assert 0 < srv.max_bytes <= budget                  # the budget held at every admission
     alone = {r.rid: r for r in serve.run_plain([reqs[0], reqs[1], reqs[3]], keep_fields=True)}
     for rid in (0, 1, 3):
         assert res[rid].status == "done"
