@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace lbm {
 
 constexpr int Q = 9;
@@ -353,58 +355,77 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
   const ColNb cn = make_col(xp, g);
 
+  const int tgi = has_tg ? tg : t;           // ghost target, own column when there is none
+  using Checked = std::true_type;            // rows may wrap, lie beyond a wall or be wall rows
+  using Inner = std::false_type;             // every touched row is interior (no checks)
+
   // store field F of row r (slot offset so) plus its mirrored ghost copies
-  auto put = [&](int so, int r, int F, float v) {
+  auto put = [&](int so, int r, int F, float v, auto checked) {
     ring[so + F * NT + t] = v;
-    const bool wrow = is_wall_row(r);
-    if (has_tg | wrow) {
-      if (has_tg) ring[so + F * NT + tg] = v;
-      if (wrow) {
+    ring[so + F * NT + tgi] = v;             // a second store to the own column when no ghost
+    if constexpr (decltype(checked)::value) {
+      if (is_wall_row(r)) {
         const int gs = ghost_slot(r);
         ring[gs + F * NT + t] = v;
-        if (has_tg) ring[gs + F * NT + tg] = v;
+        ring[gs + F * NT + tgi] = v;
       }
     }
   };
 
   // prefetched gathers: f (+ f_0lo) of the next S0 row, gbar of the next S2 row
   float fp[NF], gp[Q];
-  auto fetch_f = [&](int r) {
-    const RowNb rn = make_row(wrap1(r, g.ny), g);
+  auto row_nb = [&](int r, auto checked) {
+    if constexpr (decltype(checked)::value) {
+      return make_row(wrap1(r, g.ny), g);
+    } else {
+      RowNb rn;
+      rn.r0 = r * g.pitch;
+      rn.rm = rn.r0 - g.pitch;
+      rn.rq = rn.r0 + g.pitch;
+      rn.wb = rn.wt = false;
+      return rn;
+    }
+  };
+  auto fetch_f = [&](int r, auto checked) {
+    const RowNb rn = row_nb(r, checked);
     gather9<ST, 0>(g.src, g.plane, cn, rn, g.isf, fp);
     fp[Q] = ST == ST_FP32 ? ld_pop<ST>(g.src, g.plane, PLANE_F0LO, rn.r0 + cn.x0, 1.0f) : 0.0f;
   };
-  auto fetch_g = [&](int r) {
-    const RowNb rn = make_row(wrap1(r, g.ny), g);
+  auto fetch_g = [&](int r, auto checked) {
+    const RowNb rn = row_nb(r, checked);
     gather9<ST, Q>(g.src, g.plane, cn, rn, g.isg, gp);
   };
   auto s0_active = [&](int r) { return r <= yb + 2 && in_w3 && row_ok(r); };
   auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
-  if (s0_active(ya - 3)) fetch_f(ya - 3);
+  if (s0_active(ya - 3)) fetch_f(ya - 3, Checked{});
 
   Rec cur{}, prev{};
   int fslot = 0;                             // (a - ya + 3) mod RING_F: ring slot of row a
-  for (int a = ya - 3; a <= yb + 4; ++a) {
-    // slot offsets of the rows this iteration touches (a-7 .. a)
+  // One row iteration.  Inner iterations (every stage active, every touched row interior) drop
+  // all row tests; the fetches then run for every thread (their columns are always in range).
+  auto iter = [&](int a, auto inner_tag) {
+    constexpr bool IN = !decltype(inner_tag)::value;
+    using CK = decltype(inner_tag);
+    // slot offsets of the rows this iteration touches (a-6 .. a)
     const int o0 = slot(a), o1 = slot(a - 1), o2 = slot(a - 2), o3 = slot(a - 3);
     const int o4 = slot(a - 4), o5 = slot(a - 5), o6 = slot(a - 6);
     // ---- S0: phi at row a (as an unevaluated pair hi + lo)
-    if (s0_active(a)) {
+    if (IN ? in_w3 : s0_active(a)) {
       const float small = fp[Q] + (((fp[1] + fp[2]) + (fp[3] + fp[4])) + ((fp[5] + fp[6]) + (fp[7] + fp[8])));
       float hi, lo;
       two_sum(fp[0], small, hi, lo);
-      put(o0, a, R_PHI_HI, hi);
-      put(o0, a, R_PHI_LO, lo);
-      if (MODE == MODE_STEP && in_w0 && a >= ya) {
+      put(o0, a, R_PHI_HI, hi, CK{});
+      put(o0, a, R_PHI_LO, lo, CK{});
+      if (MODE == MODE_STEP && in_w0 && (IN || a >= ya)) {
 #pragma unroll
         for (int k = 0; k < NFR / 2; ++k) sm.f[fslot][t][k] = make_float2(fp[2 * k + 1], fp[2 * k + 2]);
       }
     }
-    if (s0_active(a + 1)) fetch_f(a + 1);
+    if (IN || s0_active(a + 1)) fetch_f(a + 1, CK{});
     // ---- S1: mu at row a-2 (rows a-3 .. a-1 of phi)
     {
       const int r = a - 2;
-      if (r >= ya - 2 && r <= yb + 1 && in_w2 && row_ok(r)) {
+      if (IN ? in_w2 : (r >= ya - 2 && r <= yb + 1 && in_w2 && row_ok(r))) {
         const float* hs = ring + o3 + R_PHI_HI * NT + t;
         const float* h0 = ring + o2 + R_PHI_HI * NT + t;
         const float* hn = ring + o1 + R_PHI_HI * NT + t;
@@ -421,13 +442,13 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float lap = (4.0f * (dax + lax) + (ddg + ldg) - 20.0f * L) * (1.0f / 6.0f);
         const float ph = H + L;
         const float dm = (H - P.phi_star) + L, dp = (H + P.phi_star) + L;
-        put(o2, r, R_MU, P.four_beta * ph * dm * dp - P.kappa * lap);
+        put(o2, r, R_MU, P.four_beta * ph * dm * dp - P.kappa * lap, CK{});
       }
     }
     // ---- S2: u, p at row a-4 (rows a-5 .. a-3 of phi and mu)
     {
       const int r = a - 4;
-      if (s2_active(r)) {
+      if (IN ? in_w1 : s2_active(r)) {
         const float* hs = ring + o5 + R_PHI_HI * NT + t;
         const float* h0 = ring + o4 + R_PHI_HI * NT + t;
         const float* hn = ring + o3 + R_PHI_HI * NT + t;
@@ -461,9 +482,9 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float uy = (3.0f * jy + 0.5f * (fsy + gy)) * rden;
         const float drx = P.rho_prime * gphx, dry = P.rho_prime * gphy;
         const float p = m0g + (1.0f / 6.0f) * (ux * drx + uy * dry);
-        put(o4, r, R_P, p);
+        put(o4, r, R_P, p, CK{});
         if (MODE == MODE_MOMENTS) {
-          if (in_w0 && r >= ya && r < yb) {
+          if (in_w0 && (IN || (r >= ya && r < yb))) {
             const int o = r * g.pitch + xp;
             mo.phi[o] = ph;
             mo.rho[o] = rho;
@@ -472,7 +493,7 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
             mo.p[o] = p;
           }
         } else {
-          if (in_w0 && r >= ya) {
+          if (in_w0 && (IN || r >= ya)) {
 #pragma unroll
             for (int k = 0; k < Q; ++k) sm.g[r & 1][k][t] = gb[k];
           }
@@ -489,13 +510,13 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
           cur.omega_g = __fdividef(1.0f, 3.0f * muv * rrho + 0.5f);   // 1 / tau_g(phi)
         }
       }
-      if (s2_active(r + 1)) fetch_g(r + 1);
+      if (IN || s2_active(r + 1)) fetch_g(r + 1, CK{});
     }
     __syncthreads();
     // ---- S3: collide and store row a-5 (p of rows a-6 .. a-4)
     if (MODE == MODE_STEP) {
       const int r = a - 5;
-      if (r >= ya && r < yb && in_w0) {
+      if (IN ? in_w0 : (r >= ya && r < yb && in_w0)) {
         const float* qs = ring + o6 + R_P * NT + t;
         const float* q0 = ring + o5 + R_P * NT + t;
         const float* qn = ring + o4 + R_P * NT + t;
@@ -518,7 +539,15 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
     }
     prev = cur;
     fslot = fslot == RING_F - 1 ? 0 : fslot + 1;
-  }
+  };
+
+  // Inner iterations: all stages active (a in [ya+5, yb+1]) and the rows touched, a-6 .. a+2,
+  // interior: no wrap, no wall row, no row beyond a wall.
+  const int a_in0 = max(ya + 5, 5), a_in1 = min(yb + 1, g.ny - 3);
+  int a = ya - 3;
+  for (; a <= yb + 4 && a < a_in0; ++a) iter(a, Checked{});
+  for (; a <= a_in1; ++a) iter(a, Inner{});
+  for (; a <= yb + 4; ++a) iter(a, Checked{});
 }
 
 }  // namespace lbm
