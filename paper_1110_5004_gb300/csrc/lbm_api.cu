@@ -46,6 +46,13 @@ Phys make_phys(const lbm_params& p) {
   P.mu_A = (float)(p.rho_A * cs2 * (p.tau_g_A - 0.5));
   P.mu_B = (float)(p.rho_B * cs2 * (p.tau_g_B - 0.5));
   P.remove_Fa = p.remove_Fa ? 1 : 0;
+  P.kappa6 = (float)(p.kappa / 6.0);
+  P.rho_prime12 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) / 12.0);
+  P.s_coef6 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) * p.theta_M / 6.0);
+  P.mu3_B = (float)(3.0 * p.rho_B * cs2 * (p.tau_g_B - 0.5));
+  P.mu3_d = (float)(3.0 * (p.rho_A * cs2 * (p.tau_g_A - 0.5) - p.rho_B * cs2 * (p.tau_g_B - 0.5)));
+  P.keep_f = (float)(1.0 - 1.0 / p.tau_f);
+  P.of3gf = (float)(3.0 * p.theta_M / (p.tau_f - 0.5) / p.tau_f);
   return P;
 }
 

@@ -1,8 +1,9 @@
 // Ragged batches: many independent simulations (any sizes and parameters) advanced by one
 // persistent launch per time step over a work list of (simulation, strip, segment) tiles.
 // k steps are captured once as a CUDA graph of k launches and replayed while the membership is
-// unchanged.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel,
-// so a member's state is bitwise the same alone or inside any mix.
+// unchanged.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel
+// (every operation an explicit round-to-nearest intrinsic), so a member's state is bitwise the
+// same alone or inside any mix.
 #include <algorithm>
 #include <map>
 #include <new>
@@ -22,7 +23,7 @@ struct SimDesc {
 };
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
+__global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
                                               int n_work, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);

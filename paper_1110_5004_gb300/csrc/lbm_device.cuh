@@ -69,6 +69,13 @@ struct Phys {
   float three_gamma_f;  // 3 theta_M / (tau_f - 1/2)
   float mu_A, mu_B;     // dynamic viscosities rho_X cs2 (tau_g_X - 1/2)
   int remove_Fa;
+  // folded into the step kernel's arithmetic
+  float kappa6;         // kappa / 6 (the isotropic Laplacian carries 1/6)
+  float rho_prime12;    // rho' / 12 (the isotropic gradient carries 1/12)
+  float s_coef6;        // rho' theta_M / 6
+  float mu3_B, mu3_d;   // 3 mu_B and 3 (mu_A - mu_B)
+  float keep_f;         // 1 - omega_f
+  float of3gf;          // omega_f 3 Gamma_f
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
@@ -204,17 +211,35 @@ __device__ __forceinline__ void gather9(const void* __restrict__ src, int plane,
   }
 }
 
-// e_a . (vx, vy) with the zero and unit components folded at compile time.
+// Every floating-point operation of the step is an explicit round-to-nearest intrinsic, so no
+// multiply-add contraction is left to the compiler: the inlined tile body computes bit for bit
+// the same in the single-simulation kernel and in the batch kernel.
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// e_a . v from the precomputed projections vx, vy, vx + vy, vx - vy (no arithmetic).
 template <int A>
-__device__ __forceinline__ float edot(float vx, float vy) {
-  constexpr int ex = cx(A), ey = cy(A);
-  const float tx = ex == 0 ? 0.0f : (ex > 0 ? vx : -vx);
-  return ey == 0 ? tx : (ex == 0 ? (ey > 0 ? vy : -vy) : (ey > 0 ? tx + vy : tx - vy));
+__device__ __forceinline__ float eproj(float vx, float vy, float vp, float vm) {
+  return A == 1 ? vx : A == 2 ? vy : A == 3 ? -vx : A == 4 ? -vy : A == 5 ? vp : A == 6 ? -vm : A == 7 ? -vp : vm;
+}
+
+// Isotropic gradient of a 3x3 stencil, times 12: rows s (south), 0, n (north), columns -1, 0, +1.
+//   12 dq/dx = 4 (E - W) + (NE - NW) + (SE - SW) = 4 (E - W) + (d1 - d2)
+//   12 dq/dy = 4 (N - S) + (NE - SE) + (NW - SW) = 4 (N - S) + (d1 + d2),  d1 = NE - SW, d2 = NW - SE
+__device__ __forceinline__ void grad12(const float* s, const float* c, const float* n, float& gx, float& gy) {
+  const float d1 = fsub(n[1], s[-1]), d2 = fsub(n[-1], s[1]);
+  gx = fmad(4.0f, fsub(c[1], c[-1]), fsub(d1, d2));
+  gy = fmad(4.0f, fsub(n[0], s[0]), fadd(d1, d2));
 }
 
 // Per-cell record carried from S2 to S3 in registers.
 struct Rec {
-  float phi, mu, rho, ux, uy, Fx, Fy, drx, dry, omega_g;
+  float phi, mu, ux, uy, Fx, Fy;
+  float mrx3, mry3;     // -(grad rho) / 3
+  float og;             // omega_g = 1 / tau_g(phi)
+  float ogr3;           // omega_g rho / 3
 };
 
 constexpr int RING = 8;      // rows of phi (hi, lo), mu and p, incl. one mirrored ghost row at a wall
@@ -234,81 +259,111 @@ struct Smem {
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 
-// One direction of both collisions.  With Gamma_a = omega_a(u) = w_a (1 + poly_a):
-//   g^eq_a = w_a p + rho cs2 (Gamma_a - w_a)
-//   S_a    = (e_a - u).[F Gamma_a - (Gamma_a - w_a) grad psi]
-//          = (e_a.F - u.F) Gamma_a - (e_a.grad psi - u.grad psi) (Gamma_a - w_a)
-//   gbar*_a = gbar_a - omega_g (gbar_a - g^eq_a) + (1 - omega_g/2) S_a
-//   f^eq_a = w_a (3 Gamma_f mu + phi poly_a)  (a > 0),   f*_a = f_a - omega_f (f_a - f^eq_a)
+// Both collisions at one cell.  With Gamma_a = omega_a(u) = w_a (1 + poly_a),
+// poly_a = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u, gmw_a = Gamma_a - w_a = w_a poly_a, D = F - grad psi:
+//   g^eq_a = w_a p + (rho / 3) gmw_a
+//   S_a    = (e_a - u).[F Gamma_a - gmw_a grad psi] = w_a (e_a.F - u.F) + gmw_a (e_a.D - u.D)
+//   gbar*_a = (1 - omega_g) gbar_a + omega_g g^eq_a + (1 - omega_g / 2) S_a
+//   f*_a   = (1 - omega_f) f_a + omega_f w_a (3 Gamma_f mu + phi poly_a)          (a > 0)
+// The weight-class products are formed once per cell (class 0: rest, 1: axis, 2: diagonal).
 struct CollideC {
-  float ux, uy, uu15, Fx, Fy, uF, Px, Py, uP, rho3, p, og, keep_g, src_g, of, keep_f, gmu, phi;
+  float ux, uy, up, um, m15uu;
+  float Fx, Fy, Fp, Fm;
+  float Dx, Dy, Dp, Dm, uD;
+  float wuF[3];     // -w_c u.F
+  float A[3];       // omega_g w_c p
+  float ogr3, keep_g, src_g, keep_f;
+  float ofwg[3];    // omega_f w_c 3 Gamma_f mu
+  float ofwp[3];    // omega_f w_c phi
 };
 
 template <int ST, int A>
 __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q], const float gb[Q], const Grid& g,
-                                            int cell, float& fsum, float& feqsum) {
+                                            int cell, float& fsum, float& ofeqsum) {
+  constexpr int C = A == 0 ? 0 : (A <= 4 ? 1 : 2);
   constexpr float w = wgt(A);
-  const float eu = edot<A>(k.ux, k.uy);
-  const float poly = A == 0 ? -k.uu15 : eu * (3.0f + 4.5f * eu) - k.uu15;
-  const float gmw = w * poly;
-  const float gam = w + gmw;
-  const float geq = w * k.p + k.rho3 * gmw;
-  const float S = A == 0 ? (-k.uF) * gam + k.uP * gmw
-                         : (edot<A>(k.Fx, k.Fy) - k.uF) * gam - (edot<A>(k.Px, k.Py) - k.uP) * gmw;
-  st_pop<ST>(g.dst, g.plane, Q + A, cell, k.keep_g * gb[A] + k.og * geq + k.src_g * S, g.sg);
+  float poly, t1w, t2;
+  if (A == 0) {
+    poly = k.m15uu;
+    t1w = k.wuF[0];
+    t2 = -k.uD;
+  } else {
+    const float eu = eproj<A>(k.ux, k.uy, k.up, k.um);
+    poly = fmad(eu, fmad(4.5f, eu, 3.0f), k.m15uu);
+    t1w = fmad(w, eproj<A>(k.Fx, k.Fy, k.Fp, k.Fm), k.wuF[C]);
+    t2 = fsub(eproj<A>(k.Dx, k.Dy, k.Dp, k.Dm), k.uD);
+  }
+  const float gmw = fmul(w, poly);
+  const float S = fmad(gmw, t2, t1w);
+  st_pop<ST>(g.dst, g.plane, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
   if (A > 0) {
-    const float feq = w * (k.gmu + k.phi * poly);
-    fsum += f[A];
-    feqsum += feq;
-    st_pop<ST>(g.dst, g.plane, A, cell, k.keep_f * f[A] + k.of * feq, g.sf);
+    const float ofeq = fmad(k.ofwp[C], poly, k.ofwg[C]);
+    fsum = fadd(fsum, f[A]);
+    ofeqsum = fadd(ofeqsum, ofeq);
+    st_pop<ST>(g.dst, g.plane, A, cell, fmad(k.keep_f, f[A], ofeq), g.sf);
   }
 }
 
 // Collision of both distributions at one cell and store of the post-collision populations.
-// f[] holds f_0..f_8 and f_0lo (index Q), gb[] gbar_0..gbar_8.
+// f[] holds f_1..f_8 (index 0 unused), gb[] gbar_0..gbar_8; gpx12/gpy12 are 12 grad p.
 template <int ST>
-__device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx, float gpy, float phi_hi,
-                                              float phi_lo, const float f[Q], const float gb[Q], const Grid& g,
-                                              int cell) {
+__device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx12, float gpy12,
+                                              float phi_hi, float phi_lo, const float f[Q], const float gb[Q],
+                                              const Grid& g, int cell) {
   CollideC k;
   k.ux = r.ux;
   k.uy = r.uy;
-  k.uu15 = 1.5f * (r.ux * r.ux + r.uy * r.uy);
+  k.up = fadd(r.ux, r.uy);
+  k.um = fsub(r.ux, r.uy);
+  k.m15uu = fmul(-1.5f, fmad(r.ux, r.ux, fmul(r.uy, r.uy)));
   k.Fx = r.Fx;
   k.Fy = r.Fy;
-  k.uF = r.ux * r.Fx + r.uy * r.Fy;
-  k.Px = gpx - (1.0f / 3.0f) * r.drx;   // grad psi = grad p - cs2 grad rho
-  k.Py = gpy - (1.0f / 3.0f) * r.dry;
-  k.uP = r.ux * k.Px + r.uy * k.Py;
-  k.rho3 = r.rho * (1.0f / 3.0f);
-  k.p = p;
-  k.og = r.omega_g;
-  k.keep_g = 1.0f - r.omega_g;
-  k.src_g = 1.0f - 0.5f * r.omega_g;
-  k.of = P.omega_f;
-  k.keep_f = 1.0f - P.omega_f;
-  k.gmu = P.three_gamma_f * r.mu;
-  k.phi = r.phi;
-  float fsum = 0.0f, feqsum = 0.0f;
-  collide_dir<ST, 0>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 1>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 2>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 3>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 4>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 5>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 6>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 7>(k, f, gb, g, cell, fsum, feqsum);
-  collide_dir<ST, 8>(k, f, gb, g, cell, fsum, feqsum);
-  // f_0 = phi - sum_{a>0} f_a and f_0^eq - f_0 = sum_{a>0} (f_a - f^eq_a), so
-  // f*_0 = phi_hi + [(phi_lo - sum f_a) + omega_f (sum f_a - sum f^eq_a)]: only small terms are
-  // rounded before the one error-free sum with the O(1) high word.
+  k.Fp = fadd(r.Fx, r.Fy);
+  k.Fm = fsub(r.Fx, r.Fy);
+  // grad psi = grad p - cs2 grad rho
+  k.Dx = fsub(r.Fx, fmad(gpx12, 1.0f / 12.0f, r.mrx3));
+  k.Dy = fsub(r.Fy, fmad(gpy12, 1.0f / 12.0f, r.mry3));
+  k.Dp = fadd(k.Dx, k.Dy);
+  k.Dm = fsub(k.Dx, k.Dy);
+  k.uD = fmad(r.ux, k.Dx, fmul(r.uy, k.Dy));
+  const float uF = fmad(r.ux, r.Fx, fmul(r.uy, r.Fy));
+  k.wuF[0] = fmul(-4.0f / 9.0f, uF);
+  k.wuF[1] = fmul(-1.0f / 9.0f, uF);
+  k.wuF[2] = fmul(-1.0f / 36.0f, uF);
+  const float ogp = fmul(r.og, p);
+  k.A[0] = fmul(4.0f / 9.0f, ogp);
+  k.A[1] = fmul(1.0f / 9.0f, ogp);
+  k.A[2] = fmul(1.0f / 36.0f, ogp);
+  k.ogr3 = r.ogr3;
+  k.keep_g = fsub(1.0f, r.og);
+  k.src_g = fmad(-0.5f, r.og, 1.0f);
+  k.keep_f = P.keep_f;
+  const float ofg = fmul(P.of3gf, r.mu), ofp = fmul(P.omega_f, r.phi);
+  k.ofwg[0] = k.ofwp[0] = 0.0f;
+  k.ofwg[1] = fmul(1.0f / 9.0f, ofg);
+  k.ofwg[2] = fmul(1.0f / 36.0f, ofg);
+  k.ofwp[1] = fmul(1.0f / 9.0f, ofp);
+  k.ofwp[2] = fmul(1.0f / 36.0f, ofp);
+  float fsum = 0.0f, ofeqsum = 0.0f;
+  collide_dir<ST, 0>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 1>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 2>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 3>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 4>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 5>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 6>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 7>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 8>(k, f, gb, g, cell, fsum, ofeqsum);
+  // f_0 = phi - sum_{a>0} f_a and omega_f (f_0^eq - f_0) = omega_f sum_{a>0} f_a - sum omega_f f^eq_a,
+  // so f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum omega_f f^eq_a)]: only small
+  // terms are rounded before the one error-free sum with the O(1) high word.
   float hi, lo;
-  two_sum(phi_hi, (phi_lo - fsum) + P.omega_f * (fsum - feqsum), hi, lo);
+  two_sum(phi_hi, fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), hi, lo);
   if (ST == ST_FP32) {
     st_pop<ST>(g.dst, g.plane, 0, cell, hi, 1.0f);
     st_pop<ST>(g.dst, g.plane, PLANE_F0LO, cell, lo, 1.0f);
   } else {
-    st_pop<ST>(g.dst, g.plane, 0, cell, hi + lo, 1.0f);
+    st_pop<ST>(g.dst, g.plane, 0, cell, fadd(hi, lo), 1.0f);
   }
 }
 
@@ -320,10 +375,9 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
 // thread that computes a value next to a wall also stores it into that ghost slot, so no read
 // is remapped.  Only one ghost row/column is ever read because every stage runs on real cells
 // and the stencils have radius 1.
-// Not inlined: the single-simulation kernel and the batch kernel call one compiled body, so
-// their arithmetic (including every multiply-add contraction) is identical by construction.
+// Inlined into both kernels; its arithmetic is fixed by the explicit intrinsics above.
 template <int NT, int MODE, int ST>
-__device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
+__device__ __forceinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
                                       Smem<NT>& sm) {
   const int t = threadIdx.x;
   const int x0 = strip * g.tile_w;
@@ -411,7 +465,8 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
     const int o4 = slot(a - 4), o5 = slot(a - 5), o6 = slot(a - 6);
     // ---- S0: phi at row a (as an unevaluated pair hi + lo)
     if (IN ? in_w3 : s0_active(a)) {
-      const float small = fp[Q] + (((fp[1] + fp[2]) + (fp[3] + fp[4])) + ((fp[5] + fp[6]) + (fp[7] + fp[8])));
+      const float small =
+          fadd(fp[Q], fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8]))));
       float hi, lo;
       two_sum(fp[0], small, hi, lo);
       put(o0, a, R_PHI_HI, hi, CK{});
@@ -435,14 +490,14 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float H = h0[0], L = l0[0];
         // differences from the centre: exact for neighbouring values of like magnitude; the low
         // words are tiny and are summed directly
-        const float dax = (h0[1] - H) + (hn[0] - H) + ((h0[-1] - H) + (hs[0] - H));
-        const float ddg = ((hn[1] - H) + (hn[-1] - H)) + ((hs[-1] - H) + (hs[1] - H));
-        const float lax = (l0[1] + ln[0]) + (l0[-1] + ls[0]);
-        const float ldg = (ln[1] + ln[-1]) + (ls[-1] + ls[1]);
-        const float lap = (4.0f * (dax + lax) + (ddg + ldg) - 20.0f * L) * (1.0f / 6.0f);
-        const float ph = H + L;
-        const float dm = (H - P.phi_star) + L, dp = (H + P.phi_star) + L;
-        put(o2, r, R_MU, P.four_beta * ph * dm * dp - P.kappa * lap, CK{});
+        const float dax = fadd(fadd(fsub(h0[1], H), fsub(hn[0], H)), fadd(fsub(h0[-1], H), fsub(hs[0], H)));
+        const float ddg = fadd(fadd(fsub(hn[1], H), fsub(hn[-1], H)), fadd(fsub(hs[-1], H), fsub(hs[1], H)));
+        const float lax = fadd(fadd(l0[1], ln[0]), fadd(l0[-1], ls[0]));
+        const float ldg = fadd(fadd(ln[1], ln[-1]), fadd(ls[-1], ls[1]));
+        const float lap6 = fmad(-20.0f, L, fmad(4.0f, fadd(dax, lax), fadd(ddg, ldg)));   // 6 lap(phi)
+        const float ph = fadd(H, L);
+        const float dm = fadd(fsub(H, P.phi_star), L), dp = fadd(fadd(H, P.phi_star), L);
+        put(o2, r, R_MU, fmad(-P.kappa6, lap6, fmul(fmul(fmul(P.four_beta, ph), dm), dp)), CK{});
       }
     }
     // ---- S2: u, p at row a-4 (rows a-5 .. a-3 of phi and mu)
@@ -456,32 +511,36 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float* m0 = ring + o4 + R_MU * NT + t;
         const float* mn = ring + o3 + R_MU * NT + t;
         // grad phi only feeds grad rho (density and pressure terms): the high words suffice
-        const float ph = h0[0] + ring[o4 + R_PHI_LO * NT + t];
-        const float gphx = (4.0f * (h0[1] - h0[-1]) + ((hn[1] - hn[-1]) + (hs[1] - hs[-1]))) * (1.0f / 12.0f);
-        const float gphy = (4.0f * (hn[0] - hs[0]) + ((hn[1] - hs[1]) + (hn[-1] - hs[-1]))) * (1.0f / 12.0f);
-        const float gmx = (4.0f * (m0[1] - m0[-1]) + ((mn[1] - mn[-1]) + (ms[1] - ms[-1]))) * (1.0f / 12.0f);
-        const float gmy = (4.0f * (mn[0] - ms[0]) + ((mn[1] - ms[1]) + (mn[-1] - ms[-1]))) * (1.0f / 12.0f);
-        const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
-        const float rho = P.rho_B + cl * P.drho;
-        const float fsx = -ph * gmx;
-        const float fsy = -ph * gmy;
-        const float gy = -rho * P.gravity;
+        const float ph = fadd(h0[0], ring[o4 + R_PHI_LO * NT + t]);
+        float gphx, gphy, gmx, gmy;                // 12 x the isotropic gradients
+        grad12(hs, h0, hn, gphx, gphy);
+        grad12(ms, m0, mn, gmx, gmy);
+        const float cl = __saturatef(fmad(ph, P.inv_2phistar, 0.5f));   // clamp((phi + phi*) / (2 phi*))
+        const float rho = fmad(cl, P.drho, P.rho_B);
+        const float mph12 = fmul(ph, -1.0f / 12.0f);
+        const float fsx = fmul(mph12, gmx);        // F_s = -phi grad mu
+        const float fsy = fmul(mph12, gmy);
+        const float gy = fmul(-P.gravity, rho);
         float sdef = 0.0f;
         if (P.remove_Fa) {
-          const float lmu = (4.0f * (m0[1] + mn[0] + m0[-1] + ms[0]) + (mn[1] + mn[-1] + ms[-1] + ms[1]) -
-                             20.0f * m0[0]) * (1.0f / 6.0f);
-          sdef = P.s_coef * lmu;
+          const float lmu6 = fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
+                                                     fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
+          sdef = fmul(P.s_coef6, lmu6);
         }
         const float* gb = gp;
-        const float m0g = ((gb[0] + gb[1]) + (gb[2] + gb[3])) + ((gb[4] + gb[5]) + (gb[6] + gb[7])) + gb[8];
-        const float jx = (gb[1] - gb[3]) + (gb[5] - gb[6]) + (gb[8] - gb[7]);
-        const float jy = (gb[2] - gb[4]) + (gb[5] + gb[6]) - (gb[7] + gb[8]);
+        const float s13 = fadd(gb[1], gb[3]), d13 = fsub(gb[1], gb[3]);
+        const float s24 = fadd(gb[2], gb[4]), d24 = fsub(gb[2], gb[4]);
+        const float s57 = fadd(gb[5], gb[7]), d57 = fsub(gb[5], gb[7]);
+        const float s68 = fadd(gb[6], gb[8]), d86 = fsub(gb[8], gb[6]);
+        const float m0g = fadd(fadd(fadd(gb[0], s13), fadd(s24, s57)), s68);
+        const float jx = fadd(fadd(d13, d57), d86);
+        const float jy = fsub(fadd(d24, d57), d86);
         const float rrho = __fdividef(1.0f, rho);
-        const float rden = P.remove_Fa ? __fdividef(1.0f, rho - 0.5f * sdef) : rrho;
-        const float ux = (3.0f * jx + 0.5f * fsx) * rden;
-        const float uy = (3.0f * jy + 0.5f * (fsy + gy)) * rden;
-        const float drx = P.rho_prime * gphx, dry = P.rho_prime * gphy;
-        const float p = m0g + (1.0f / 6.0f) * (ux * drx + uy * dry);
+        const float rden = P.remove_Fa ? __fdividef(1.0f, fmad(-0.5f, sdef, rho)) : rrho;
+        const float ux = fmul(fmad(3.0f, jx, fmul(0.5f, fsx)), rden);
+        const float uy = fmul(fmad(3.0f, jy, fmul(0.5f, fadd(fsy, gy))), rden);
+        const float rx = fmul(P.rho_prime12, gphx), ry = fmul(P.rho_prime12, gphy);   // grad rho
+        const float p = fmad(fmad(ux, rx, fmul(uy, ry)), 1.0f / 6.0f, m0g);
         put(o4, r, R_P, p, CK{});
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && (IN || (r >= ya && r < yb))) {
@@ -499,15 +558,15 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
           }
           cur.phi = ph;
           cur.mu = m0[0];
-          cur.rho = rho;
           cur.ux = ux;
           cur.uy = uy;
-          cur.Fx = fsx + (P.remove_Fa ? ux * sdef : 0.0f);
-          cur.Fy = fsy + gy + (P.remove_Fa ? uy * sdef : 0.0f);
-          cur.drx = drx;
-          cur.dry = dry;
-          const float muv = P.mu_B + cl * (P.mu_A - P.mu_B);
-          cur.omega_g = __fdividef(1.0f, 3.0f * muv * rrho + 0.5f);   // 1 / tau_g(phi)
+          cur.Fx = P.remove_Fa ? fmad(ux, sdef, fsx) : fsx;
+          cur.Fy = P.remove_Fa ? fmad(uy, sdef, fadd(fsy, gy)) : fadd(fsy, gy);
+          cur.mrx3 = fmul(-1.0f / 3.0f, rx);
+          cur.mry3 = fmul(-1.0f / 3.0f, ry);
+          const float muv3 = fmad(cl, P.mu3_d, P.mu3_B);                  // 3 mu(phi)
+          cur.og = __fdividef(1.0f, fmad(muv3, rrho, 0.5f));              // 1 / tau_g(phi)
+          cur.ogr3 = fmul(cur.og, fmul(rho, 1.0f / 3.0f));
         }
       }
       if (IN || s2_active(r + 1)) fetch_g(r + 1, CK{});
@@ -520,8 +579,8 @@ __device__ __noinline__ void run_tile(const Phys P, const Grid g, const MomentOu
         const float* qs = ring + o6 + R_P * NT + t;
         const float* q0 = ring + o5 + R_P * NT + t;
         const float* qn = ring + o4 + R_P * NT + t;
-        const float gpx = (4.0f * (q0[1] - q0[-1]) + ((qn[1] - qn[-1]) + (qs[1] - qs[-1]))) * (1.0f / 12.0f);
-        const float gpy = (4.0f * (qn[0] - qs[0]) + ((qn[1] - qs[1]) + (qn[-1] - qs[-1]))) * (1.0f / 12.0f);
+        float gpx, gpy;                          // 12 grad p
+        grad12(qs, q0, qn, gpx, gpy);
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
         float f[Q], gb[Q];
         f[0] = 0.0f;   // unused: f_0 follows from the phi pair

@@ -9,7 +9,8 @@ namespace lbm {
 // ------------------------------------------------------------------ fused step / moments
 
 template <int NT, int MODE, int ST>
-__global__ void __launch_bounds__(NT) k_tiles(Phys P, Grid g, MomentOut mo) {
+// 512 / NT resident CTAs per SM (16 warps): caps the registers at 128 per thread.
+__global__ void __launch_bounds__(NT, 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
   const int strip = blockIdx.x % g.n_strips;
