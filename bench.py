@@ -253,6 +253,36 @@ def serve_leg(args, lbm, torch):
             "served": served, "plain_back_to_back": plain}
 
 
+def other_grids(lbm, torch, peak):
+    """Secondary lines: a 4096 x 4096 periodic static drop (2.4 GB ping-pong, far above L2) and the
+    L2-resident c1 / c2 grids, each with its autotuned tile, timed over consecutive steps (no
+    flush: the large grid does not fit in L2, the small ones are labelled L2-resident)."""
+    import workloads as W
+    from paper_1110_5004_gb300 import autotune
+    stream = torch.cuda.current_stream()
+    out = {}
+    for key, w, steps, label in (("large_grid", W.static_droplet(nx=4096, ny=4096, R=600.0), 20, "exceeds L2"),
+                                 ("c1", W.static_droplet(), 400, "L2-resident"),
+                                 ("c2", W.falling_droplet(), 40, "L2-resident; re-initialised before timing")):
+        sim = lbm.Sim.from_workload(w, stream=stream)
+        t_, r_, _ = autotune.tune_sim(sim, reps=3)
+        sim.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
+        sim.step(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(steps)
+        b.record(stream)
+        b.synchronize()
+        dt = a.elapsed_time(b) * 1e-3 / steps
+        mlups = w.cells / dt / 1e6
+        out[key] = {"workload": w.name, "cells": w.cells, "mlups": mlups, "us_per_step": dt * 1e6,
+                    "hbm_frac_of_measured": B_MIN_FP32 * mlups * 1e6 / (peak * 1e9), "tile": [t_, r_],
+                    "note": label}
+        sim.close()
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -384,8 +414,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_steps)
 
-    batch = serving = None
+    batch = serving = others = None
     if not args.quick:
+        others = other_grids(lbm, torch, peak)
         import workloads as W
         batch = batch_leg(args, lbm, torch)
         ws = W.ragged_batch(n=args.batch_sims, steps=args.batch_steps)
@@ -413,7 +444,8 @@ def run_ours(args):
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,
                 "batch": batch,
-                "serving": serving}
+                "serving": serving,
+                "other_grids": others}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

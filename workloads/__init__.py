@@ -200,6 +200,26 @@ def paper_falling_droplet(steps=19000, remove_Fa=0):
                 yc=yc)
 
 
+def paper_splash(Re=480.0, steps=3000, remove_Fa=0):
+    """The paper's first experiment at its own size: droplet splashing on a thin film, 300x150,
+    film height one tenth of the domain height, We = 960 with sigma = 1e-4, U = 0.04, D = 60;
+    Re = 48 or 480 (nu_L = 0.05 or 0.005); W = 3, rho_L = 1, rho_G = 0.1.  The paper gives one
+    viscosity: both phases take nu_L.  Walls on y, periodic in x; the drop touches the film and
+    moves down at U."""
+    nx, ny, D, U, sigma = 300, 150, 60.0, 0.04, 1e-4
+    nu = U * D / Re
+    h, W = 0.1 * ny, 3.0
+    phys = Physical(sigma=sigma, W=W, nu_A=nu, nu_B=nu, rho_A=1.0, rho_B=0.1, gravity=0.0,
+                    bc_x=PERIODIC, bc_y=WALL, remove_Fa=remove_Fa)
+    R = D / 2
+    yc = h + R + W
+    drop = droplet_phi(nx, ny, nx / 2, yc, R, W, periodic_y=False)
+    phi0 = np.maximum(drop, film_phi(nx, ny, h, W))
+    uy0 = np.where(drop >= 0.0, -U, 0.0)
+    return make("paper_splash_300x150_Re%g" % Re, nx, ny, phys, steps, phi0, uy0=uy0, R=R, xc=nx / 2,
+                yc=yc, h=h, U=U, D=D)
+
+
 def _round32(v):
     return max(32, int(round(v / 32.0)) * 32)
 
