@@ -74,10 +74,18 @@ extern "C" {
  *   remove_Fa     0: scheme as first stated (Eq. 8 with F_s + G);
  *                 1: additional interfacial force removed (forcing F_s + G + u s with
  *                    s = rho' theta_M lap(mu) = d_t rho + div(rho u) by Eq. 5).
- *   storage       LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV. */
+ *   storage       LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV.
+ *   ch_conservative  0 (default): the f collision adds w_a phi div(u) (div by the isotropic
+ *                 central differences), so the recovered Cahn-Hilliard equation is Eq. 2's
+ *                 convective form d_t phi + u.grad(phi) = div(theta_M grad mu) even where the
+ *                 weakly compressible flow has div(u) != 0;
+ *                 1: no source, the conservative form d_t phi + div(phi u) = ... (the f
+ *                 collision conserves phi locally).
+ *   pad           set to 0. */
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
+    int ch_conservative, pad;
 } lbm_params;
 
 /* FP64 diagnostics of the current state (reductions in a fixed order: bitwise reproducible).

@@ -26,7 +26,12 @@
  *   gbar_a(x + e_a, t+1) = gbar_a - (gbar_a - g^eq_a)/tau_g + (1 - 1/(2 tau_g)) S_a
  *   f^eq_a (a != 0) = w_a [Gamma_f mu / cs2 + phi (e.u/cs2 + (e.u)^2/(2 cs2^2) - u^2/(2 cs2))],
  *   f^eq_0 = phi - sum_{a != 0} f^eq_a,  Gamma_f = theta_M / (tau_f - 1/2)   (recovers Eq. 2)
- *   f_a(x + e_a, t+1) = f_a - (f_a - f^eq_a)/tau_f
+ *   f_a(x + e_a, t+1) = f_a - (f_a - f^eq_a)/tau_f + w_a phi div(u)   [convective form]
+ *   The moments of f^eq make the f-LBE recover d_t phi + div(phi u) = div(theta_M grad mu);
+ *   Eq. 2 is the convective form d_t phi + u.grad(phi) = div(theta_M grad mu).  The two differ
+ *   by phi div(u), which the weakly compressible flow does not make zero; the source
+ *   w_a phi div(u) (zeroth moment phi div(u), div by the isotropic central differences) turns
+ *   the recovered equation into Eq. 2.  ch_conservative = 1 drops it (conservative form).
  * Boundaries: periodic, or a no-slip wall half a cell outside the first/last row (column):
  *   links that would leave through the wall are reversed in place (half-way bounce-back), and
  *   stencils see mirrored ghost values (zero normal gradient of phi, mu and p).
@@ -56,6 +61,8 @@ static const double CS2 = 1.0 / 3.0;
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
+    int ch_conservative;    /* 0: convective Cahn-Hilliard (Eq. 2), 1: conservative form */
+    int pad;
 } orc_params;
 
 typedef struct {
@@ -74,6 +81,7 @@ typedef struct {
     /* per-cell work fields, [ny][nx] */
     double *phi, *mu, *lap, *rho, *gpx, *gpy, *gmx, *gmy, *lmu;
     double *fsx, *fsy, *gy, *s, *ux, *uy, *p, *dpx, *dpy;
+    double *divu, *w1, *w2;  /* div(u) and gradient scratch */
 } orc_sim;
 
 static int opposite(int a) {
@@ -226,7 +234,8 @@ void lbm_destroy_ref(orc_sim* s) {
     if (!s) return;
     double** fields[] = {&s->f, &s->g, &s->fs, &s->gs, &s->phi, &s->mu, &s->lap, &s->rho,
                          &s->gpx, &s->gpy, &s->gmx, &s->gmy, &s->lmu, &s->fsx, &s->fsy,
-                         &s->gy, &s->s, &s->ux, &s->uy, &s->p, &s->dpx, &s->dpy};
+                         &s->gy, &s->s, &s->ux, &s->uy, &s->p, &s->dpx, &s->dpy,
+                         &s->divu, &s->w1, &s->w2};
     for (size_t i = 0; i < sizeof(fields) / sizeof(fields[0]); ++i) free(*fields[i]);
     free(s);
 }
@@ -253,7 +262,7 @@ int lbm_create_ref(int nx, int ny, const orc_params* P, orc_sim** out) {
     s->gs = alloc_field(Q * N);
     double** fields[] = {&s->phi, &s->mu, &s->lap, &s->rho, &s->gpx, &s->gpy, &s->gmx, &s->gmy,
                          &s->lmu, &s->fsx, &s->fsy, &s->gy, &s->s, &s->ux, &s->uy, &s->p,
-                         &s->dpx, &s->dpy};
+                         &s->dpx, &s->dpy, &s->divu, &s->w1, &s->w2};
     int ok = s->f && s->g && s->fs && s->gs;
     for (size_t i = 0; i < sizeof(fields) / sizeof(fields[0]); ++i) {
         *fields[i] = alloc_field(N);
@@ -343,6 +352,15 @@ static void compute_moments(orc_sim* s) {
     }
 }
 
+/* div(u) by the isotropic central differences: d(ux)/dx + d(uy)/dy. */
+static void divergence(orc_sim* s) {
+    const orc_params* P = &s->P;
+    size_t N = (size_t)s->nx * s->ny;
+    orc_grad_iso(s->nx, s->ny, P->bc_x, P->bc_y, s->ux, s->divu, s->w1);
+    orc_grad_iso(s->nx, s->ny, P->bc_x, P->bc_y, s->uy, s->w1, s->w2);
+    for (size_t i = 0; i < N; ++i) s->divu[i] += s->w2[i];
+}
+
 /* Post-collision populations of the current state, no streaming. */
 static void collide(orc_sim* s) {
     const orc_params* P = &s->P;
@@ -350,6 +368,7 @@ static void collide(orc_sim* s) {
     size_t N = (size_t)nx * ny;
     compute_moments(s);
     orc_grad_iso(nx, ny, P->bc_x, P->bc_y, s->p, s->dpx, s->dpy);
+    divergence(s);
     double rp = drho_dphi(P);
     double tf = P->tau_f;
 #pragma omp parallel for schedule(static)
@@ -372,7 +391,7 @@ static void collide(orc_sim* s) {
             double gv = s->g[a * N + i];
             s->gs[a * N + i] = gv - (gv - geq[a]) / tg + (1.0 - 1.0 / (2.0 * tg)) * S[a];
             double fv = s->f[a * N + i];
-            s->fs[a * N + i] = fv - (fv - feq[a]) / tf;
+            s->fs[a * N + i] = fv - (fv - feq[a]) / tf + (P->ch_conservative ? 0.0 : WT[a] * ph * s->divu[i]);
         }
     }
 }
@@ -426,13 +445,14 @@ int lbm_moments_ref(orc_sim* s, double* phi, double* rho, double* ux, double* uy
 
 /* Named work fields of the current state (after lbm_moments_ref / a collision). */
 enum { ORC_MU = 0, ORC_S = 1, ORC_FSX = 2, ORC_FSY = 3, ORC_DPX = 4, ORC_DPY = 5,
-       ORC_GRAD_PHI_X = 6, ORC_GRAD_PHI_Y = 7, ORC_LAP_MU = 8, ORC_TAU_G = 9 };
+       ORC_GRAD_PHI_X = 6, ORC_GRAD_PHI_Y = 7, ORC_LAP_MU = 8, ORC_TAU_G = 9, ORC_DIVU = 10 };
 
 int orc_field(orc_sim* s, int which, double* out) {
     if (!s || !out) return -1;
     size_t N = (size_t)s->nx * s->ny;
     compute_moments(s);
     orc_grad_iso(s->nx, s->ny, s->P.bc_x, s->P.bc_y, s->p, s->dpx, s->dpy);
+    divergence(s);
     const double* src = NULL;
     switch (which) {
         case ORC_MU: src = s->mu; break;
@@ -444,6 +464,7 @@ int orc_field(orc_sim* s, int which, double* out) {
         case ORC_GRAD_PHI_X: src = s->gpx; break;
         case ORC_GRAD_PHI_Y: src = s->gpy; break;
         case ORC_LAP_MU: src = s->lmu; break;
+        case ORC_DIVU: src = s->divu; break;
         case ORC_TAU_G:
             for (size_t i = 0; i < N; ++i) out[i] = tau_g_of(&s->P, s->phi[i]);
             return 0;

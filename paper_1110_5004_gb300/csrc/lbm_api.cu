@@ -46,6 +46,7 @@ Phys make_phys(const lbm_params& p) {
   P.mu_A = (float)(p.rho_A * cs2 * (p.tau_g_A - 0.5));
   P.mu_B = (float)(p.rho_B * cs2 * (p.tau_g_B - 0.5));
   P.remove_Fa = p.remove_Fa ? 1 : 0;
+  P.ch_conv = p.ch_conservative ? 0 : 1;
   P.kappa6 = (float)(p.kappa / 6.0);
   P.rho_prime12 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) / 12.0);
   P.s_coef6 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) * p.theta_M / 6.0);
@@ -116,6 +117,8 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("theta_M must be >= 0 and gravity finite"), LBM_ERR_INVALID_ARG;
   if (p->storage != LBM_FP32 && p->storage != LBM_FP16_DEV && p->storage != LBM_BF16_DEV)
     return set_error("storage must be LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV"), LBM_ERR_INVALID_ARG;
+  if (p->ch_conservative != 0 && p->ch_conservative != 1)
+    return set_error("ch_conservative must be 0 or 1"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 

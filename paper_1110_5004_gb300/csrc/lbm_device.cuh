@@ -76,6 +76,7 @@ struct Phys {
   float mu3_B, mu3_d;   // 3 mu_B and 3 (mu_A - mu_B)
   float keep_f;         // 1 - omega_f
   float of3gf;          // omega_f 3 Gamma_f
+  int ch_conv;          // 1: the f collision adds w_a phi div(u) (convective Cahn-Hilliard form)
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
@@ -243,6 +244,8 @@ struct Rec {
 };
 
 constexpr int RING = 8;      // rows of phi (hi, lo), mu and p, incl. one mirrored ghost row at a wall
+constexpr int RING_U = 4;    // rows of u_x, u_y (written by S2 at a-4, read by S3 at a-6 .. a-4),
+                             // plus two slots for the mirrored ghost rows beyond walls
 constexpr int RING_F = 6;    // f rows a-5..a awaiting S3 (thread-private)
 constexpr int NF = Q + 1;    // gathered f_0..f_8 and f_0lo
 constexpr int NFR = 8;       // f_1..f_8 kept for S3: f_0 is rebuilt there from the phi pair
@@ -253,6 +256,7 @@ enum { R_PHI_HI = 0, R_PHI_LO = 1, R_MU = 2, R_P = 3, R_FIELDS = 4 };
 template <int NT>
 struct Smem {
   float rows[RING][R_FIELDS][NT];  // phi (hi, lo), mu, p of recent rows
+  float urows[RING_U + 2][2][NT];  // u_x, u_y of recent rows (convective form only)
   float2 f[RING_F][NT][NFR / 2];   // own column only (no barrier needed); 64-bit accesses
   float g[2][Q][NT];               // own column only
 };
@@ -264,7 +268,7 @@ enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 //   g^eq_a = w_a p + (rho / 3) gmw_a
 //   S_a    = (e_a - u).[F Gamma_a - gmw_a grad psi] = w_a (e_a.F - u.F) + gmw_a (e_a.D - u.D)
 //   gbar*_a = (1 - omega_g) gbar_a + omega_g g^eq_a + (1 - omega_g / 2) S_a
-//   f*_a   = (1 - omega_f) f_a + omega_f w_a (3 Gamma_f mu + phi poly_a)          (a > 0)
+//   f*_a   = (1 - omega_f) f_a + omega_f w_a (3 Gamma_f mu + phi poly_a) + w_a phi div(u)   (a > 0)
 // The weight-class products are formed once per cell (class 0: rest, 1: axis, 2: diagonal).
 struct CollideC {
   float ux, uy, up, um, m15uu;
@@ -306,10 +310,11 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
 
 // Collision of both distributions at one cell and store of the post-collision populations.
 // f[] holds f_1..f_8 (index 0 unused), gb[] gbar_0..gbar_8; gpx12/gpy12 are 12 grad p.
+// phiD = phi div(u) (convective form) or 0: the f collision adds w_a phiD to direction a.
 template <int ST>
 __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx12, float gpy12,
-                                              float phi_hi, float phi_lo, const float f[Q], const float gb[Q],
-                                              const Grid& g, int cell) {
+                                              float phi_hi, float phi_lo, float phiD, const float f[Q],
+                                              const float gb[Q], const Grid& g, int cell) {
   CollideC k;
   k.ux = r.ux;
   k.uy = r.uy;
@@ -338,7 +343,7 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   k.keep_g = fsub(1.0f, r.og);
   k.src_g = fmad(-0.5f, r.og, 1.0f);
   k.keep_f = P.keep_f;
-  const float ofg = fmul(P.of3gf, r.mu), ofp = fmul(P.omega_f, r.phi);
+  const float ofg = fadd(fmul(P.of3gf, r.mu), phiD), ofp = fmul(P.omega_f, r.phi);
   k.ofwg[0] = k.ofwp[0] = 0.0f;
   k.ofwg[1] = fmul(1.0f / 9.0f, ofg);
   k.ofwg[2] = fmul(1.0f / 36.0f, ofg);
@@ -354,11 +359,13 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   collide_dir<ST, 6>(k, f, gb, g, cell, fsum, ofeqsum);
   collide_dir<ST, 7>(k, f, gb, g, cell, fsum, ofeqsum);
   collide_dir<ST, 8>(k, f, gb, g, cell, fsum, ofeqsum);
-  // f_0 = phi - sum_{a>0} f_a and omega_f (f_0^eq - f_0) = omega_f sum_{a>0} f_a - sum omega_f f^eq_a,
-  // so f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum omega_f f^eq_a)]: only small
-  // terms are rounded before the one error-free sum with the O(1) high word.
+  // f_0 = phi - sum_{a>0} f_a and omega_f (f_0^eq - f_0) = omega_f sum_{a>0} f_a - sum omega_f f^eq_a;
+  // the directions a > 0 carry w_a phiD of the source inside ofeqsum, so the rest gets
+  // phiD - (5/9) phiD = w_0 phiD by adding phiD:
+  // f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum (omega_f f^eq_a + w_a phiD)) + phiD].
+  // Only small terms are rounded before the one error-free sum with the O(1) high word.
   float hi, lo;
-  two_sum(phi_hi, fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), hi, lo);
+  two_sum(phi_hi, fadd(fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), phiD), hi, lo);
   if (ST == ST_FP32) {
     st_pop<ST>(g.dst, g.plane, 0, cell, hi, 1.0f);
     st_pop<ST>(g.dst, g.plane, PLANE_F0LO, cell, lo, 1.0f);
@@ -408,6 +415,14 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto is_wall_row = [&](int r) { return ywall && (r == 0 || r == g.ny - 1); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
   const ColNb cn = make_col(xp, g);
+  constexpr int USLOT = 2 * NT;
+  float* const uring = &sm.urows[0][0][0];
+  // Ring slot of row r; the ghost rows beyond a wall (-1, ny) have slots of their own, since a
+  // 4-row ring would put the top one on a row that S3 of the previous iteration still reads.
+  auto uslot = [&](int r) { return (r & (RING_U - 1)) * USLOT; };
+  auto uslot_ck = [&](int r) {
+    return ywall && r < 0 ? RING_U * USLOT : (ywall && r >= g.ny ? (RING_U + 1) * USLOT : uslot(r));
+  };
 
   const int tgi = has_tg ? tg : t;           // ghost target, own column when there is none
   using Checked = std::true_type;            // rows may wrap, lie beyond a wall or be wall rows
@@ -422,6 +437,24 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const int gs = ghost_slot(r);
         ring[gs + F * NT + t] = v;
         ring[gs + F * NT + tgi] = v;
+      }
+    }
+  };
+
+  // u_x, u_y of row r with the same mirrored ghost copies
+  auto put_u = [&](int r, float ux, float uy, auto checked) {
+    const int so = uslot(r);
+    uring[so + t] = ux;
+    uring[so + tgi] = ux;
+    uring[so + NT + t] = uy;
+    uring[so + NT + tgi] = uy;
+    if constexpr (decltype(checked)::value) {
+      if (is_wall_row(r)) {
+        const int gs = r == 0 ? RING_U * USLOT : (RING_U + 1) * USLOT;
+        uring[gs + t] = ux;
+        uring[gs + tgi] = ux;
+        uring[gs + NT + t] = uy;
+        uring[gs + NT + tgi] = uy;
       }
     }
   };
@@ -542,6 +575,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const float rx = fmul(P.rho_prime12, gphx), ry = fmul(P.rho_prime12, gphy);   // grad rho
         const float p = fmad(fmad(ux, rx, fmul(uy, ry)), 1.0f / 6.0f, m0g);
         put(o4, r, R_P, p, CK{});
+        if (MODE == MODE_STEP && P.ch_conv) put_u(r, ux, uy, CK{});
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && (IN || (r >= ya && r < yb))) {
             const int o = r * g.pitch + xp;
@@ -581,6 +615,18 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const float* qn = ring + o4 + R_P * NT + t;
         float gpx, gpy;                          // 12 grad p
         grad12(qs, q0, qn, gpx, gpy);
+        float phiD = 0.0f;                       // phi div(u) of the convective form
+        if (P.ch_conv) {
+          const float* xs_ = uring + (IN ? uslot(a - 6) : uslot_ck(a - 6)) + t;
+          const float* x0_ = uring + uslot(a - 5) + t;
+          const float* xn_ = uring + (IN ? uslot(a - 4) : uslot_ck(a - 4)) + t;
+          const float* ys_ = xs_ + NT;
+          const float* yn_ = xn_ + NT;
+          // 12 d(ux)/dx = 4 (E - W) + (NE - SW) - (NW - SE);  12 d(uy)/dy = 4 (N - S) + (NE - SW) + (NW - SE)
+          const float dux = fmad(4.0f, fsub(x0_[1], x0_[-1]), fsub(fsub(xn_[1], xs_[-1]), fsub(xn_[-1], xs_[1])));
+          const float duy = fmad(4.0f, fsub(yn_[0], ys_[0]), fadd(fsub(yn_[1], ys_[-1]), fsub(yn_[-1], ys_[1])));
+          phiD = fmul(prev.phi, fmul(fadd(dux, duy), 1.0f / 12.0f));
+        }
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
         float f[Q], gb[Q];
         f[0] = 0.0f;   // unused: f_0 follows from the phi pair
@@ -592,8 +638,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
-        collide_store<ST>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], f,
-                          gb, g, r * g.pitch + xp);
+        collide_store<ST>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], phiD,
+                          f, gb, g, r * g.pitch + xp);
       }
     }
     prev = cur;
@@ -601,8 +647,9 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   };
 
   // Inner iterations: all stages active (a in [ya+5, yb+1]) and the rows touched, a-6 .. a+2,
-  // interior: no wrap, no wall row, no row beyond a wall.
-  const int a_in0 = max(ya + 5, 5), a_in1 = min(yb + 1, g.ny - 3);
+  // interior: no wrap, no wall row, no row beyond a wall (a - 6 >= 0 keeps the u ring's own
+  // ghost slots out of inner iterations).
+  const int a_in0 = max(ya + 5, 6), a_in1 = min(yb + 1, g.ny - 3);
   int a = ya - 3;
   for (; a <= yb + 4 && a < a_in0; ++a) iter(a, Checked{});
   for (; a <= a_in1; ++a) iter(a, Inner{});

@@ -9,6 +9,8 @@ index or weight anywhere in the oracle breaks at least one of them.
 import math
 import os
 
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -116,6 +118,19 @@ def test_forcing_moments(seed):
     assert (EY * S).sum() == pytest.approx(CS2 * Fy, abs=1e-15)
 
 
+def iso_div(ux, uy, bcx, bcy):
+    """div(u) with the isotropic central differences, written out here with numpy padding
+    (periodic: wrap; wall half a cell outside: mirror, -1 -> 0)."""
+    def pad(a):
+        a = np.pad(a, ((0, 0), (1, 1)), mode="wrap" if bcx == W.PERIODIC else "symmetric")
+        return np.pad(a, ((1, 1), (0, 0)), mode="wrap" if bcy == W.PERIODIC else "symmetric")
+    X, Y = pad(ux), pad(uy)
+    c = slice(1, -1)
+    dx = (4 * (X[c, 2:] - X[c, :-2]) + (X[2:, 2:] - X[2:, :-2]) + (X[:-2, 2:] - X[:-2, :-2])) / 12
+    dy = (4 * (Y[2:, c] - Y[:-2, c]) + (Y[2:, 2:] - Y[:-2, 2:]) + (Y[2:, :-2] - Y[:-2, :-2])) / 12
+    return dx + dy
+
+
 @pytest.mark.parametrize("remove_Fa", [0, 1])
 def test_collision_momentum_impulse(remove_Fa):
     """The collision adds the full force impulse: sum_a e_a (gbar*_a - gbar_a) = cs2 F at every
@@ -135,8 +150,33 @@ def test_collision_momentum_impulse(remove_Fa):
     imp_y = np.tensordot(EY, gst - g, axes=1)
     np.testing.assert_allclose(imp_x, CS2 * Fx, atol=1e-15)
     np.testing.assert_allclose(imp_y, CS2 * Fy, atol=1e-15)
-    # the f collision conserves phi locally
-    np.testing.assert_allclose(fst.sum(0), f.sum(0), atol=1e-14)
+    # the f collision changes phi locally by the convective-form source phi div(u) only
+    np.testing.assert_allclose(fst.sum(0) - f.sum(0), m["phi"] * iso_div(m["ux"], m["uy"], w.phys.bc_x, w.phys.bc_y),
+                               atol=1e-14)
+
+
+@pytest.mark.parametrize("bcy", [W.PERIODIC, W.WALL])
+def test_convective_source_and_conservative_form(bcy):
+    """Eq. 2 is the convective form: on one and the same state, the f collision with
+    ch_conservative = 0 differs from the conservative form (ch_conservative = 1) by exactly w_a phi div(u) per
+    direction; gbar is untouched, and the conservative form conserves phi locally."""
+    w1 = W.random_small(26, 18, seed=11, bc_y=bcy, gravity=2e-5 if bcy == W.WALL else 0.0, ratio=5.0)
+    w0 = dataclasses.replace(w1, phys=dataclasses.replace(w1.phys, ch_conservative=1))
+    s1 = oracle.Sim.from_workload(w1)
+    s1.step(7)
+    f, g = s1.get_state()
+    s0 = oracle.Sim.from_workload(w0)
+    s0.set_state(f, g)
+    m = s1.moments()
+    div = iso_div(m["ux"], m["uy"], w1.phys.bc_x, w1.phys.bc_y)
+    np.testing.assert_allclose(s1.field(oracle.DIVU), div, atol=1e-15)
+    fst1, gst1 = s1.collide()
+    fst0, gst0 = s0.collide()
+    assert np.array_equal(gst1, gst0)
+    wts = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    np.testing.assert_allclose(fst1 - fst0, wts[:, None, None] * (m["phi"] * div)[None], atol=1e-15)
+    np.testing.assert_allclose(fst0.sum(0), f.sum(0), atol=1e-14)
+    np.testing.assert_allclose(fst1.sum(0) - f.sum(0), m["phi"] * div, atol=1e-14)
 
 
 # ----------------------------------------------------------------- stencils
@@ -223,14 +263,22 @@ def test_streaming_brute_force(bc_x, bc_y):
 
 @pytest.mark.parametrize("bc_y,remove_Fa", [(0, 0), (0, 1), (1, 0), (1, 1)])
 def test_total_phi_conserved(bc_y, remove_Fa):
-    """Eq. 5 integrated: total phi is constant on periodic or walled boxes (BGK conserves
-    sum_a f_a at each node and streaming/bounce-back only moves populations)."""
-    w = W.random_small(33, 17, seed=11, bc_y=bc_y, remove_Fa=remove_Fa, gravity=1e-5 * bc_y)
-    s = oracle.Sim.from_workload(w)
-    s0 = s.moments()["phi"].sum()
-    for _ in range(10):
-        s.step(20)
-        assert abs(s.moments()["phi"].sum() - s0) <= 1e-12 * w.cells
+    """Eq. 5 integrated, conservative form: total phi is constant on periodic or walled boxes
+    (BGK conserves sum_a f_a at each node and streaming/bounce-back only moves populations).
+    Convective form (Eq. 2): each step changes total phi by exactly sum phi div(u) of the state
+    it starts from (the source), div(u) taken with the test's own stencil."""
+    for ch in (0, 1):
+        w = W.random_small(33, 17, seed=11, bc_y=bc_y, remove_Fa=remove_Fa, gravity=1e-5 * bc_y)
+        w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, ch_conservative=1 - ch))
+        s = oracle.Sim.from_workload(w)
+        m = s.moments()
+        s0 = m["phi"].sum()
+        for _ in range(20):
+            src = (m["phi"] * iso_div(m["ux"], m["uy"], w.phys.bc_x, w.phys.bc_y)).sum() if ch else 0.0
+            s.step(1)
+            m = s.moments()
+            assert abs(m["phi"].sum() - s0 - src) <= 1e-12 * w.cells
+            s0 = m["phi"].sum()
 
 
 def test_transpose_symmetry():
@@ -356,17 +404,21 @@ def test_laplace_law():
         assert dp == pytest.approx(sigma / R, rel=0.05)
 
 
-def test_linear_cahn_hilliard_decay():
-    """Eq. 2 linearised about a uniform phi0 (theta''(phi0) > 0) and coupled to the pressure
-    equation Eq. 9.  A mode cos(kx) has mu' = M phi' with M = theta''(phi0) + kappa lam,
-    lam = 2 (1 - cos k) the discrete Laplacian symbol.  Force balance grad(p) = -phi0 grad(mu')
-    with d_t p = -rho cs2 div(u) (Eq. 9) gives a flow whose flux phi0 u slows the decay:
-        rate = theta_M lam M / (1 + phi0^2 M / (rho cs2)),
-    theta_M = Gamma_f (tau_f - 1/2) being the mobility of the Cahn-Hilliard equilibrium.
-    Checked within 2 % after the acoustic transient."""
+@pytest.mark.parametrize("ch", [1, 0])
+def test_linear_cahn_hilliard_decay(ch):
+    """Eq. 2 linearised about a uniform phi0 (theta''(phi0) > 0).  A mode cos(kx) has
+    mu' = M phi' with M = theta''(phi0) + kappa lam, lam = 2 (1 - cos k) the discrete Laplacian
+    symbol.
+    Convective form (Eq. 2 as printed, ch_conservative = 0): u.grad(phi) is second order, so the mode
+    decays at the Cahn-Hilliard rate theta_M lam M.
+    Conservative form (ch_conservative = 1): force balance grad(p) = -phi0 grad(mu') with
+    d_t p = -rho cs2 div(u) (Eq. 9) gives a flow whose flux phi0 u slows the decay:
+        rate = theta_M lam M / (1 + phi0^2 M / (rho cs2)).
+    theta_M = Gamma_f (tau_f - 1/2) is the mobility of the Cahn-Hilliard equilibrium.  Checked
+    within 2 % after the acoustic transient; the two forms differ by ~27 % here."""
     nx, ny, phi0, eps = 32, 4, 0.8, 1e-4
     sigma, Wd, thM, rho = 0.1, 2.0, 0.1, 1.0
-    phys = W.Physical(sigma=sigma, W=Wd, theta_M=thM, rho_A=rho, rho_B=rho)
+    phys = W.Physical(sigma=sigma, W=Wd, theta_M=thM, rho_A=rho, rho_B=rho, ch_conservative=1 - ch)
     k = 2 * np.pi / nx
     xs = np.arange(nx)
     phi = phi0 + eps * np.cos(k * xs)[None, :].repeat(ny, 0)
@@ -374,7 +426,8 @@ def test_linear_cahn_hilliard_decay():
     beta, kappa = oracle.params_from_sigma_W(sigma, Wd)
     lam = 2 * (1 - np.cos(k))
     M = 4 * beta * (3 * phi0 ** 2 - 1) + kappa * lam
-    rate = thM * lam * M / (1 + phi0 ** 2 * M / (rho * CS2))
+    plain = thM * lam * M
+    rate = plain if ch else plain / (1 + phi0 ** 2 * M / (rho * CS2))
     amps, ts = [], []
     s.step(1500)
     for t in range(6):
@@ -384,8 +437,9 @@ def test_linear_cahn_hilliard_decay():
         s.step(300)
     fit = -np.polyfit(ts, np.log(amps), 1)[0]
     assert fit == pytest.approx(rate, rel=0.02)
-    # without the compressible coupling the prediction would be ~20 % off: the pin sees Eq. 9
-    assert abs(fit / (thM * lam * M) - 1) > 0.1
+    if not ch:
+        # without the compressible coupling the prediction would be ~20 % off: the pin sees Eq. 9
+        assert abs(fit / plain - 1) > 0.1
 
 
 @pytest.mark.parametrize("phase", [+1, -1])
@@ -429,18 +483,20 @@ def test_hydrostatic_pressure_under_gravity():
         assert np.abs(m["uy"]).max() < 0.05 * g
 
 
-def test_mass_defect_matches_finite_differences():
-    """Eq. 5: d_t rho + div(rho u) = rho' div(theta_M grad mu) = s.  The oracle's s is checked
-    against an independent space-time finite-difference evaluation of
-    rho' (d_t phi + div(phi u)) on smooth periodic fields, i.e. the recovered Cahn-Hilliard
-    equation (Eq. 2, conservative form); the residual is far below |s|.  (The density form
-    d_t rho + div(rho u) itself differs from s by (rho_A + rho_B)/2 div(u), the weak
-    compressibility of Eq. 9, which on this field is larger than s.)"""
+@pytest.mark.parametrize("ch", [1, 0])
+def test_mass_defect_matches_finite_differences(ch):
+    """Eq. 5: d_t rho + div(rho u) = rho' (d_t phi + u.grad phi) = rho' div(theta_M grad mu) = s.
+    The oracle's s is checked against an independent space-time finite-difference evaluation
+    of the recovered Cahn-Hilliard equation on smooth periodic fields: rho' (d_t phi + u.grad phi)
+    for the convective form (Eq. 2 as printed, ch_conservative = 0), rho' (d_t phi + div(phi u)) for the
+    conservative form (ch_conservative = 1); the residual is far below |s|.  (The density form
+    d_t rho + div(rho u) itself differs from s by the weak compressibility of Eq. 9, which on
+    this field is larger than s.)"""
     n = 64
     y, x = np.mgrid[0:n, 0:n].astype(float)
     phi = 0.75 + 0.15 * np.sin(2 * np.pi * x / n) * np.sin(2 * np.pi * y / n) + \
         0.05 * np.cos(4 * np.pi * x / n)
-    phys = W.Physical(sigma=0.05, W=6.0, theta_M=0.1, rho_A=1.0, rho_B=0.5)
+    phys = W.Physical(sigma=0.05, W=6.0, theta_M=0.1, rho_A=1.0, rho_B=0.5, ch_conservative=1 - ch)
     s = oracle.Sim.from_workload(W.make("fd", n, n, phys, 0, phi))
     s.step(3000)    # past the acoustic transient
     rp = (phys.rho_A - phys.rho_B) / 2
@@ -457,7 +513,11 @@ def test_mass_defect_matches_finite_differences():
     def ddy(a):
         return (np.roll(a, -1, 0) - np.roll(a, 1, 0)) / 2
 
-    fd = rp * ((m_next["phi"] - m_prev["phi"]) / 2 + ddx(m["phi"] * m["ux"]) + ddy(m["phi"] * m["uy"]))
+    if ch:
+        adv = m["ux"] * ddx(m["phi"]) + m["uy"] * ddy(m["phi"])
+    else:
+        adv = ddx(m["phi"] * m["ux"]) + ddy(m["phi"] * m["uy"])
+    fd = rp * ((m_next["phi"] - m_prev["phi"]) / 2 + adv)
     scale = np.abs(sdef).max()
     assert scale > 1e-7
     assert np.abs(fd - sdef).max() < 0.05 * scale

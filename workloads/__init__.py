@@ -60,6 +60,7 @@ class Physical:
     bc_x: int = PERIODIC
     bc_y: int = PERIODIC
     remove_Fa: int = 0      # 0: scheme as first stated, 1: additional interfacial force removed
+    ch_conservative: int = 0  # 0: convective Cahn-Hilliard equation (as printed), 1: conservative form
 
 
 @dataclasses.dataclass
