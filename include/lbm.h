@@ -147,6 +147,22 @@ LBM_API int lbm_destroy(lbm_sim* sim);
 /* Number of time steps taken since lbm_init_fields. */
 LBM_API long long lbm_step_count(const lbm_sim* sim);
 
+/* Checkpoint / resume (no counterpart in the paper: it lets a server evict a simulation's
+ * device state to host memory and resume it later bitwise).  A checkpoint is a 64-byte header
+ * (magic "LBMC", version 1, nx, ny, row pitch, storage, step count, payload size) followed by
+ * the raw population buffer of the current state; it holds no parameters.
+ * lbm_checkpoint_bytes: size of the checkpoint of `sim` (0 if sim is NULL).
+ * lbm_checkpoint: writes it to `buf` (host or device memory, at least checkpoint_bytes long,
+ *   caller-owned); synchronous.  A batch member must be removed from its batch first.
+ * lbm_restore: replaces the state of `sim` (same nx, ny and storage; its parameters and stream
+ *   are its own) by the checkpoint in `buf`, including the step count; synchronous.
+ * Errors: LBM_ERR_INVALID_ARG for NULL arguments, a short buffer, a batch member, a bad header
+ * or a size/storage mismatch (the state is then left unchanged); LBM_ERR_CUDA for copy
+ * failures. */
+LBM_API size_t lbm_checkpoint_bytes(const lbm_sim* sim);
+LBM_API int lbm_checkpoint(lbm_sim* sim, void* buf, size_t bytes);
+LBM_API int lbm_restore(lbm_sim* sim, const void* buf, size_t bytes);
+
 /* Replace the stream the simulation queues its work on (cudaStream_t, may be NULL). */
 LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
 

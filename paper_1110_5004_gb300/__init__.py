@@ -35,6 +35,19 @@ def _ptr(a):
     return a.data_ptr()
 
 
+def _bptr(a):
+    """Address of any C-contiguous host numpy array or contiguous device torch tensor."""
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous, "C-contiguous array required"
+        return a.ctypes.data
+    assert a.is_contiguous(), "contiguous tensor required"
+    return a.data_ptr()
+
+
+def _nbytes(a):
+    return int(a.nbytes) if isinstance(a, np.ndarray) else int(a.numel() * a.element_size())
+
+
 def _stream_handle(stream):
     if stream is None:
         return None
@@ -114,6 +127,23 @@ class Sim:
     @property
     def launch_count(self):
         return int(lib().lbm_launch_count(self._h))
+
+    @property
+    def checkpoint_bytes(self):
+        return int(lib().lbm_checkpoint_bytes(self._h))
+
+    def checkpoint(self, out=None):
+        """The current state as a checkpoint: into `out` (a host array or a device tensor of at
+        least checkpoint_bytes bytes) or a new uint8 host array."""
+        n = self.checkpoint_bytes
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        _lib.check(lib().lbm_checkpoint(self._h, _bptr(out), _nbytes(out)))
+        return out
+
+    def restore(self, buf):
+        """Replace the state (and step count) by a checkpoint of a same-sized simulation."""
+        _lib.check(lib().lbm_restore(self._h, _bptr(buf), _nbytes(buf)))
 
     def moments(self, out=None):
         """phi, rho, ux, uy, p as (ny, nx) float32 host arrays (or into the given dict of

@@ -23,7 +23,8 @@ EXPORTS = (
     "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_destroy", "lbm_step_count", "lbm_set_stream",
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
-    "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile",
+    "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
+    "lbm_checkpoint", "lbm_restore",
 )
 
 
@@ -72,6 +73,9 @@ def load(path: str = LIB_PATH):
         "lbm_diagnostics": (ip, [vp, ctypes.POINTER(lbm_diag)]),
         "lbm_destroy": (ip, [vp]),
         "lbm_step_count": (ctypes.c_longlong, [vp]),
+        "lbm_checkpoint_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_checkpoint": (ip, [vp, vp, ctypes.c_size_t]),
+        "lbm_restore": (ip, [vp, vp, ctypes.c_size_t]),
         "lbm_set_stream": (ip, [vp, vp]),
         "lbm_set_tile": (ip, [vp, ip, ip]),
         "lbm_launch_count": (ctypes.c_longlong, [vp]),

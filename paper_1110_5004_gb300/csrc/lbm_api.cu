@@ -297,6 +297,74 @@ int lbm_destroy(lbm_sim* s) {
 
 long long lbm_step_count(const lbm_sim* s) { return s ? s->steps : -1; }
 
+}  // extern "C"
+
+namespace {
+struct CkptHeader {
+  uint32_t magic;       // "LBMC"
+  uint32_t version;     // 1
+  int32_t nx, ny, pitch, storage;
+  int64_t steps;
+  uint64_t payload;     // bytes of the population buffer that follows
+  uint64_t reserved[3];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+constexpr uint32_t CKPT_MAGIC = 0x434d424cu;   // "LBMC" little-endian
+
+size_t payload_bytes(const lbm_sim* s) { return (size_t)state_bytes_per_cell(s->params.storage) * s->plane; }
+}  // namespace
+
+extern "C" {
+
+size_t lbm_checkpoint_bytes(const lbm_sim* s) { return s ? sizeof(CkptHeader) + payload_bytes(s) : 0; }
+
+int lbm_checkpoint(lbm_sim* s, void* buf, size_t bytes) {
+  if (!s || !buf) return set_error("sim and buf are required"), LBM_ERR_INVALID_ARG;
+  if (s->batch) return set_error("remove the simulation from its batch before a checkpoint"), LBM_ERR_INVALID_ARG;
+  if (bytes < lbm_checkpoint_bytes(s))
+    return set_error("checkpoint buffer of %zu bytes, %zu needed", bytes, lbm_checkpoint_bytes(s)), LBM_ERR_INVALID_ARG;
+  CkptHeader h{};
+  h.magic = CKPT_MAGIC;
+  h.version = 1;
+  h.nx = s->nx;
+  h.ny = s->ny;
+  h.pitch = s->pitch;
+  h.storage = s->params.storage;
+  h.steps = s->steps;
+  h.payload = payload_bytes(s);
+  const bool dev = is_device_ptr(buf);
+  const cudaMemcpyKind kh = dev ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+  const cudaMemcpyKind kp = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaError_t e = cudaMemcpyAsync(buf, &h, sizeof(h), kh, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(static_cast<char*>(buf) + sizeof(h), s->buf[s->cur], h.payload, kp, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);   // h lives on this stack frame
+  return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_checkpoint copy");
+}
+
+int lbm_restore(lbm_sim* s, const void* buf, size_t bytes) {
+  if (!s || !buf) return set_error("sim and buf are required"), LBM_ERR_INVALID_ARG;
+  if (s->batch) return set_error("remove the simulation from its batch before a restore"), LBM_ERR_INVALID_ARG;
+  if (bytes < sizeof(CkptHeader)) return set_error("checkpoint shorter than its header"), LBM_ERR_INVALID_ARG;
+  const bool dev = is_device_ptr(buf);
+  CkptHeader h{};
+  cudaError_t e = cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_restore header");
+  if (h.magic != CKPT_MAGIC || h.version != 1) return set_error("not a checkpoint (bad magic or version)"), LBM_ERR_INVALID_ARG;
+  if (h.nx != s->nx || h.ny != s->ny || h.pitch != s->pitch || h.storage != s->params.storage ||
+      h.payload != payload_bytes(s))
+    return set_error("checkpoint of a %dx%d storage-%d grid, simulation is %dx%d storage %d", h.nx, h.ny, h.storage,
+                     s->nx, s->ny, s->params.storage), LBM_ERR_INVALID_ARG;
+  if (bytes < sizeof(h) + h.payload) return set_error("checkpoint truncated"), LBM_ERR_INVALID_ARG;
+  e = cudaMemcpyAsync(s->buf[s->cur], static_cast<const char*>(buf) + sizeof(h), h.payload,
+                      dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_restore copy");
+  s->steps = h.steps;
+  return LBM_OK;
+}
+
 int lbm_set_stream(lbm_sim* s, void* stream) {
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
   s->stream = (cudaStream_t)stream;

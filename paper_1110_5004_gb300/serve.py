@@ -7,9 +7,15 @@ tiles of all members).  Between rounds the server
   - retires members that reached their step count (FP64 diagnostics and, optionally, the
     moment fields copied back to the host; the member's device memory is freed),
   - retires members whose state stopped being finite (failure detection, LBM_ERR_DIVERGED),
-  - admits waiting requests, first come first served, while the device-memory budget, the
-    member cap and the cap on lattice cells in flight allow (a request larger than the whole
-    budget is rejected at once; the cell cap never blocks the only request).
+  - admits waiting requests in order of priority, then arrival, while the device-memory budget,
+    the member cap and the cap on lattice cells in flight allow (a request larger than the whole
+    budget is rejected at once; the cell cap never blocks the only request),
+  - preempts: when the request at the head of the queue does not fit and members of lower
+    priority are running, the fewest of them needed (lowest priority, latest admitted first) are
+    evicted -- removed from the batch, their state checkpointed to host memory
+    (lbm_checkpoint) and their device memory freed -- and queued again; on readmission the state
+    is restored (lbm_restore), so an evicted request ends bitwise where an uninterrupted run
+    ends.
 Latency is measured from arrival to the result being on the host.  `run_plain` serves the same
 stream back to back, one plain simulation at a time, as the baseline.
 """
@@ -31,6 +37,7 @@ class Request:
     steps: int
     arrival_s: float = 0.0
     storage: int = LBM_FP32
+    priority: int = 0         # higher is more urgent; may preempt running lower priorities
 
 
 @dataclasses.dataclass
@@ -43,6 +50,7 @@ class Result:
     finish_s: float
     diagnostics: Optional[dict] = None
     fields: Optional[Dict[str, np.ndarray]] = None
+    evictions: int = 0
 
     @property
     def latency_s(self):
@@ -64,11 +72,45 @@ def summarize(results: List[Result], wall_s: float) -> dict:
             "lattice_updates": lu, "mlups": lu / wall_s / 1e6 if wall_s > 0 else float("nan")}
 
 
-class _Member:
-    def __init__(self, req: Request, sim: Sim, slot: int, admit_s: float, check_steps: int):
-        self.req, self.sim, self.slot, self.admit_s = req, sim, slot, admit_s
+class _Pending:
+    """A queued request: new, or evicted with its checkpoint."""
+
+    def __init__(self, req: Request, check_steps: int):
+        self.req = req
         self.remaining = req.steps
         self.next_check = check_steps
+        self.ckpt = None          # host checkpoint of an evicted run
+        self.admit_s = None       # first admission
+        self.evictions = 0
+        self.seq = 0              # admission order, to pick the latest-admitted victim
+
+    def key(self):
+        return (-self.req.priority, self.req.arrival_s, self.req.rid)
+
+
+class _Member:
+    def __init__(self, pend: _Pending, sim: Sim, slot: int):
+        self.pend, self.req, self.sim, self.slot = pend, pend.req, sim, slot
+
+    @property
+    def remaining(self):
+        return self.pend.remaining
+
+    @remaining.setter
+    def remaining(self, v):
+        self.pend.remaining = v
+
+    @property
+    def next_check(self):
+        return self.pend.next_check
+
+    @next_check.setter
+    def next_check(self, v):
+        self.pend.next_check = v
+
+    @property
+    def admit_s(self):
+        return self.pend.admit_s
 
 
 class Server:
@@ -92,6 +134,8 @@ class Server:
         self.max_concurrent = 0
         self.max_bytes = 0                 # peak device bytes held by members
         self.rounds = 0
+        self.evictions = 0
+        self._seq = 0
 
     def cancel(self, rid: int):
         self.cancelled.add(rid)
@@ -101,15 +145,45 @@ class Server:
         fields = m.sim.moments() if self.keep_fields and status == "done" else None
         self.batch.remove(m.slot)
         m.sim.close()
-        r = Result(m.req.rid, status, m.req.steps - m.remaining, m.req.arrival_s, m.admit_s, now(), diag, fields)
+        r = Result(m.req.rid, status, m.req.steps - m.remaining, m.req.arrival_s, m.admit_s, now(), diag, fields,
+                   m.pend.evictions)
         r.diagnostics_cells = m.req.workload.cells
         results.append(r)
+
+    def _fits(self, r: Request, need: int, active) -> bool:
+        cells = sum(m.req.workload.cells for m in active.values())
+        return (self.batch.bytes + need <= self.budget and len(active) < self.max_members and
+                (not active or cells + r.workload.cells <= self.max_cells))
+
+    def _victims(self, r: Request, need: int, active):
+        """Fewest lower-priority members whose eviction lets r in (lowest priority, latest
+        admitted first), or None."""
+        cands = sorted((m for m in active.values() if m.req.priority < r.priority),
+                       key=lambda m: (m.req.priority, -m.pend.seq))
+        chosen, bytes_, count, cells = [], self.batch.bytes, len(active), \
+            sum(m.req.workload.cells for m in active.values())
+        for m in cands:
+            chosen.append(m)
+            bytes_ -= device_bytes(m.req.workload.nx, m.req.workload.ny, m.req.storage)
+            count -= 1
+            cells -= m.req.workload.cells
+            if bytes_ + need <= self.budget and count < self.max_members and \
+                    (count == 0 or cells + r.workload.cells <= self.max_cells):
+                return chosen
+        return None
+
+    def _evict(self, m: _Member):
+        self.batch.remove(m.slot)
+        m.pend.ckpt = m.sim.checkpoint()
+        m.sim.close()
+        m.pend.evictions += 1
+        self.evictions += 1
 
     def run(self, requests: List[Request], realtime: bool = True) -> List[Result]:
         """Serve `requests` (arrival times in seconds from the start).  With realtime=False the
         arrival clock jumps to the next arrival whenever the device would otherwise idle."""
         pending = sorted(requests, key=lambda r: r.arrival_s)
-        waiting: List[Request] = []
+        waiting: List[_Pending] = []
         active: Dict[int, _Member] = {}
         results: List[Result] = []
         t0 = time.perf_counter()
@@ -121,33 +195,51 @@ class Server:
         while pending or waiting or active:
             t = now()
             while pending and pending[0].arrival_s <= t:
-                waiting.append(pending.pop(0))
+                waiting.append(_Pending(pending.pop(0), self.check_steps))
+            waiting.sort(key=_Pending.key)
             # cancellations
-            for r in [r for r in waiting if r.rid in self.cancelled]:
-                waiting.remove(r)
-                results.append(Result(r.rid, "cancelled", 0, r.arrival_s, None, now()))
+            for w in [w for w in waiting if w.req.rid in self.cancelled]:
+                waiting.remove(w)
+                results.append(Result(w.req.rid, "cancelled", w.req.steps - w.remaining, w.req.arrival_s, w.admit_s,
+                                      now(), evictions=w.evictions))
             for m in [m for m in active.values() if m.req.rid in self.cancelled]:
                 del active[m.slot]
                 self._finish(m, "cancelled", now, results)
-            # admission, first come first served
+            # admission in priority order, preempting lower priorities when needed
             while waiting:
-                r = waiting[0]
+                w = waiting[0]
+                r = w.req
                 need = device_bytes(r.workload.nx, r.workload.ny, r.storage)
                 if need > self.budget:
                     waiting.pop(0)
                     results.append(Result(r.rid, "rejected", 0, r.arrival_s, None, now()))
                     continue
-                cells = sum(m.req.workload.cells for m in active.values())
-                if self.batch.bytes + need > self.budget or len(active) >= self.max_members or \
-                        (active and cells + r.workload.cells > self.max_cells):
-                    break
-                sim = Sim.from_workload(r.workload, storage=r.storage, stream=self.stream)
+                if not self._fits(r, need, active):
+                    victims = self._victims(r, need, active)
+                    if victims is None:
+                        break
+                    for m in victims:
+                        del active[m.slot]
+                        self._evict(m)
+                        waiting.append(m.pend)
+                    waiting.sort(key=_Pending.key)
+                    continue
+                if w.ckpt is not None:
+                    sim = Sim.from_workload(r.workload, storage=r.storage, stream=self.stream, init=False)
+                    sim.restore(w.ckpt)
+                else:
+                    sim = Sim.from_workload(r.workload, storage=r.storage, stream=self.stream)
                 slot = self.batch.try_add(sim)
                 if slot is None:            # the library's own budget check agrees with ours
                     sim.close()
                     break
                 waiting.pop(0)
-                active[slot] = _Member(r, sim, slot, now(), self.check_steps)
+                w.ckpt = None
+                if w.admit_s is None:
+                    w.admit_s = now()
+                self._seq += 1
+                w.seq = self._seq
+                active[slot] = _Member(w, sim, slot)
             self.max_concurrent = max(self.max_concurrent, len(active))
             self.max_bytes = max(self.max_bytes, self.batch.bytes)
             if not active:

@@ -16,8 +16,14 @@ class FakeSim:
         FakeSim.live += 1
 
     @classmethod
-    def from_workload(cls, w, storage=0, stream=None):
+    def from_workload(cls, w, storage=0, stream=None, init=True):
         return cls(w, w.meta.get("diverge_at"))
+
+    def checkpoint(self):
+        return {"steps": self.steps}
+
+    def restore(self, ck):
+        self.steps = ck["steps"]
 
     def diagnostics(self):
         ok = self.diverge_at is None or self.steps < self.diverge_at
@@ -56,9 +62,23 @@ class FakeBatch:
         self.history.append((k, len(self.members)))
         for s in self.members.values():
             s.steps += k
+        FakeClock.t += 1e-4 * k
 
     def close(self):
         pass
+
+
+class FakeClock:
+    """Time advances only with the batch's steps (0.1 ms per step)."""
+    t = 0.0
+
+    @classmethod
+    def perf_counter(cls):
+        return cls.t
+
+    @staticmethod
+    def sleep(dt):
+        FakeClock.t += dt
 
 
 @pytest.fixture
@@ -67,7 +87,9 @@ def fake_server(monkeypatch):
     monkeypatch.setattr(serve, "Sim", FakeSim)
     monkeypatch.setattr(serve, "Batch", FakeBatch)
     monkeypatch.setattr(serve, "device_bytes", lambda nx, ny, st=0: nx * ny)
+    monkeypatch.setattr(serve, "time", FakeClock)
     FakeSim.live = 0
+    FakeClock.t = 0.0
     return serve
 
 
@@ -106,6 +128,30 @@ def test_rejection_divergence_and_cancellation(fake_server):
     assert res[2].status == "diverged" and res[2].steps_done == 100
     assert res[3].status == "cancelled"
     assert FakeSim.live == 0
+
+
+def test_priority_preemption_checkpoints_and_resumes(fake_server):
+    serve = fake_server
+    low = [_req(serve, i, 10, 10, 1000, 0.0) for i in range(3)]
+    high = serve.Request(9, _req(serve, 9, 10, 10, 300, 0.0).workload, 300, arrival_s=0.03, priority=5)
+    srv = serve.Server(budget_bytes=200, chunk_steps=50, check_steps=100, stream=0)   # two at a time
+    res = {r.rid: r for r in srv.run(low + [high], realtime=False)}
+    assert all(r.status == "done" for r in res.values())
+    assert all(res[i].steps_done == 1000 for i in range(3)) and res[9].steps_done == 300
+    assert srv.evictions >= 1 and sum(r.evictions for r in res.values()) == srv.evictions
+    assert res[9].evictions == 0
+    # the urgent request was admitted soon after it arrived, before the low-priority backlog
+    assert res[9].admit_s < 0.04 and res[9].finish_s < res[2].finish_s
+    assert srv.max_bytes <= 200
+    assert FakeSim.live == 0
+
+
+def test_no_preemption_among_equal_priorities(fake_server):
+    serve = fake_server
+    reqs = [_req(serve, i, 10, 10, 400, 0.01 * i) for i in range(4)]
+    srv = serve.Server(budget_bytes=200, chunk_steps=50, check_steps=100, stream=0)
+    res = srv.run(reqs, realtime=False)
+    assert [r.status for r in res] == ["done"] * 4 and srv.evictions == 0
 
 
 def test_summary_percentiles(fake_server):
@@ -186,3 +232,72 @@ def test_served_budget_failure_and_cancel(lbm):
         assert res[rid].status == "done"
         assert np.array_equal(res[rid].fields["phi"], alone[rid].fields["phi"])
     srv.close()
+
+
+@pytest.mark.gpu
+def test_preempted_requests_end_bitwise_as_uninterrupted(lbm, monkeypatch):
+    """Low-priority requests evicted to host memory by an urgent one and restored later end
+    bitwise where the same requests end run alone without interruption.  The server's clock
+    advances with the batch's steps, so the urgent request arrives after 100 steps."""
+    from paper_1110_5004_gb300 import serve
+    monkeypatch.setattr(serve, "time", FakeClock)
+    FakeClock.t = 0.0
+    base = gpu_stream()[:4]
+    low = [serve.Request(r.rid, r.workload, 400, arrival_s=0.0, storage=r.storage) for r in base[:3]]
+    urgent = serve.Request(50, base[3].workload, 200, arrival_s=0.01, priority=3)
+    need = {r.rid: lbm.device_bytes(r.workload.nx, r.workload.ny, r.storage) for r in low + [urgent]}
+    # room for the largest low request next to the urgent one, not for two low ones next to it
+    budget = max(need[r.rid] for r in low) + need[50] + 1000
+    srv = serve.Server(budget_bytes=budget, chunk_steps=40, check_steps=80, keep_fields=True)
+    step = srv.batch.step
+
+    def timed_step(k):
+        step(k)
+        FakeClock.t += 1e-4 * k
+
+    srv.batch.step = timed_step
+    res = {r.rid: r for r in srv.run(low + [urgent], realtime=False)}
+    alone = {r.rid: r for r in serve.run_plain(low + [urgent], keep_fields=True, realtime=False)}
+    assert srv.evictions >= 1 and res[50].evictions == 0
+    for rid, r in res.items():
+        assert r.status == alone[rid].status == "done"
+        for k in r.fields:
+            assert np.array_equal(r.fields[k], alone[rid].fields[k]), (rid, k)
+    srv.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("storage", [0, 1])
+def test_checkpoint_restore_bitwise(lbm, storage):
+    import torch
+    w = W.random_small(83, 47, seed=21, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    a = lbm.Sim.from_workload(w, storage=storage)
+    a.step(37)
+    ck = a.checkpoint()
+    assert ck.nbytes == a.checkpoint_bytes
+    a.step(41)
+    b = lbm.Sim.from_workload(w, storage=storage, init=False)
+    b.restore(ck)
+    assert b.step_count == 37
+    b.step(41)
+    ma, mb = a.moments(), b.moments()
+    for k in ma:
+        assert np.array_equal(ma[k], mb[k]), k
+    # device-resident checkpoint buffer
+    dev = torch.empty(a.checkpoint_bytes, dtype=torch.uint8, device="cuda")
+    a.checkpoint(dev)
+    c = lbm.Sim.from_workload(w, storage=storage, init=False)
+    c.restore(dev)
+    assert c.step_count == 78 and np.array_equal(c.moments()["phi"], ma["phi"])
+    # mismatches are rejected and leave the state unchanged
+    other = lbm.Sim.from_workload(W.random_small(84, 47, seed=21), storage=storage)
+    before = other.moments()["phi"]
+    with pytest.raises(lbm.LBMError):
+        other.restore(ck)
+    bad = ck.copy()
+    bad[0] ^= 0xFF
+    with pytest.raises(lbm.LBMError):
+        b.restore(bad)
+    with pytest.raises(lbm.LBMError):
+        b.restore(ck[:100])
+    assert np.array_equal(other.moments()["phi"], before)
