@@ -81,11 +81,12 @@ extern "C" {
  *                 weakly compressible flow has div(u) != 0;
  *                 1: no source, the conservative form d_t phi + div(phi u) = ... (the f
  *                 collision conserves phi locally).
- *   pad           set to 0. */
+ *   fs_form       0 (default): surface-tension force F_s = -phi grad(mu) (the solved p is the
+ *                 modified pressure p_h - phi mu); 1: F_s = mu grad(phi) (p is p_h). */
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
-    int ch_conservative, pad;
+    int ch_conservative, fs_form;
 } lbm_params;
 
 /* FP64 diagnostics of the current state (reductions in a fixed order: bitwise reproducible).

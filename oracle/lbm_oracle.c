@@ -14,7 +14,7 @@
  *   mu    = theta'(phi) - kappa lap(phi),  theta = beta (phi^2 - phi*^2)^2           (Eq. 1, mu)
  *   rho   = rho_B + c (rho_A - rho_B),  c = (phi + phi*) / (2 phi*)  clamped to [0,1] (Eq. 4)
  *   grad, lap: isotropic central differences over the D2Q9 neighbours            (experiments)
- *   F_s   = -phi grad(mu),  G = (0, -rho g)                                        (Eq. 3)
+ *   F_s   = -phi grad(mu) (fs_form 0) or mu grad(phi) (fs_form 1),  G = (0, -rho g)  (Eq. 3)
  *   s     = rho' theta_M lap(mu)   = d_t rho + div(rho u) by Eq. 5
  *   u     = (sum_a e_a gbar_a / cs2 + (F_s + G)/2) / (rho - s/2 [corrected])
  *   p     = sum_a gbar_a + cs2 u.grad(rho) / 2
@@ -62,7 +62,7 @@ typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
     int ch_conservative;    /* 0: convective Cahn-Hilliard (Eq. 2), 1: conservative form */
-    int pad;
+    int fs_form;            /* 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi) */
 } orc_params;
 
 typedef struct {
@@ -332,8 +332,13 @@ static void compute_moments(orc_sim* s) {
         double ph = s->phi[i];
         double rho = density(P, ph);
         s->rho[i] = rho;
-        s->fsx[i] = -ph * s->gmx[i];
-        s->fsy[i] = -ph * s->gmy[i];
+        if (P->fs_form) {
+            s->fsx[i] = s->mu[i] * s->gpx[i];
+            s->fsy[i] = s->mu[i] * s->gpy[i];
+        } else {
+            s->fsx[i] = -ph * s->gmx[i];
+            s->fsy[i] = -ph * s->gmy[i];
+        }
         s->gy[i] = -rho * P->gravity;
         s->s[i] = rp * P->theta_M * s->lmu[i];
         double jx = 0.0, jy = 0.0, m0 = 0.0;

@@ -47,6 +47,7 @@ Phys make_phys(const lbm_params& p) {
   P.mu_B = (float)(p.rho_B * cs2 * (p.tau_g_B - 0.5));
   P.remove_Fa = p.remove_Fa ? 1 : 0;
   P.ch_conv = p.ch_conservative ? 0 : 1;
+  P.fs_mu = p.fs_form ? 1 : 0;
   P.kappa6 = (float)(p.kappa / 6.0);
   P.rho_prime12 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) / 12.0);
   P.s_coef6 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) * p.theta_M / 6.0);
@@ -119,6 +120,7 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("storage must be LBM_FP32, LBM_FP16_DEV or LBM_BF16_DEV"), LBM_ERR_INVALID_ARG;
   if (p->ch_conservative != 0 && p->ch_conservative != 1)
     return set_error("ch_conservative must be 0 or 1"), LBM_ERR_INVALID_ARG;
+  if (p->fs_form != 0 && p->fs_form != 1) return set_error("fs_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 

@@ -77,6 +77,7 @@ struct Phys {
   float keep_f;         // 1 - omega_f
   float of3gf;          // omega_f 3 Gamma_f
   int ch_conv;          // 1: the f collision adds w_a phi div(u) (convective Cahn-Hilliard form)
+  int fs_mu;            // 1: F_s = mu grad(phi); 0: F_s = -phi grad(mu)
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
@@ -550,9 +551,16 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         grad12(ms, m0, mn, gmx, gmy);
         const float cl = __saturatef(fmad(ph, P.inv_2phistar, 0.5f));   // clamp((phi + phi*) / (2 phi*))
         const float rho = fmad(cl, P.drho, P.rho_B);
-        const float mph12 = fmul(ph, -1.0f / 12.0f);
-        const float fsx = fmul(mph12, gmx);        // F_s = -phi grad mu
-        const float fsy = fmul(mph12, gmy);
+        float fsx, fsy;                            // F_s = -phi grad mu, or mu grad phi
+        if (P.fs_mu) {
+          const float mu12 = fmul(m0[0], 1.0f / 12.0f);
+          fsx = fmul(mu12, gphx);
+          fsy = fmul(mu12, gphy);
+        } else {
+          const float mph12 = fmul(ph, -1.0f / 12.0f);
+          fsx = fmul(mph12, gmx);
+          fsy = fmul(mph12, gmy);
+        }
         const float gy = fmul(-P.gravity, rho);
         float sdef = 0.0f;
         if (P.remove_Fa) {

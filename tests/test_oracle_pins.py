@@ -378,15 +378,18 @@ def test_planar_interface_width_and_tension():
     assert kappa * np.sum(d[sel] ** 2) == pytest.approx(sigma, rel=0.03)
 
 
-def test_laplace_law():
-    """Eq. 3 at rest: the hydrodynamic pressure p_h = p + phi mu (the solved p is the modified
-    pressure of the potential-form force -phi grad(mu)) jumps by sigma/R across a static
-    droplet.  Slope of dp_h against 1/R over four radii within 5 %."""
+@pytest.mark.parametrize("fs_form", [0, 1])
+def test_laplace_law(fs_form):
+    """Eq. 3 at rest: the hydrodynamic pressure jumps by sigma/R across a static droplet.  With
+    the potential-form force -phi grad(mu) the solved p is the modified pressure and
+    p_h = p + phi mu; with F_s = mu grad(phi) the solved p is p_h itself (the two forces differ
+    by grad(phi mu)).  Slope of dp_h against 1/R over four radii within 5 %."""
     n, Wd, sigma = 64, 4.0, 0.01
     Rs = [10.0, 12.0, 14.0, 16.0]
     dps = []
     for R in Rs:
         w = W.static_droplet(nx=n, ny=n, R=R, W=Wd, sigma=sigma, steps=0)
+        w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, fs_form=fs_form))
         s = oracle.Sim.from_workload(w)
         s.step(5000)
         acc = []
@@ -395,13 +398,38 @@ def test_laplace_law():
         for _ in range(10):
             s.step(200)
             m = s.moments()
-            ph = m["p"] + m["phi"] * s.field(oracle.MU)
+            ph = m["p"] + (0.0 if fs_form else m["phi"] * s.field(oracle.MU))
             acc.append(ph[r < R - 2 * Wd].mean() - ph[r > R + 2 * Wd].mean())
         dps.append(np.mean(acc))
     slope, icpt = np.polyfit(1.0 / np.array(Rs), np.array(dps), 1)
     assert slope == pytest.approx(sigma, rel=0.05)
     for R, dp in zip(Rs, dps):
         assert dp == pytest.approx(sigma / R, rel=0.05)
+
+
+def test_surface_force_forms():
+    """F_s = mu grad(phi) (fs_form = 1) and -phi grad(mu) (fs_form = 0), each against the
+    product of the oracle's phi and mu with the test's own isotropic gradient."""
+    def grad(a):
+        P = np.pad(a, 1, mode="wrap")
+        c = slice(1, -1)
+        gx = (4 * (P[c, 2:] - P[c, :-2]) + (P[2:, 2:] - P[2:, :-2]) + (P[:-2, 2:] - P[:-2, :-2])) / 12
+        gy = (4 * (P[2:, c] - P[:-2, c]) + (P[2:, 2:] - P[:-2, 2:]) + (P[2:, :-2] - P[:-2, :-2])) / 12
+        return gx, gy
+    for form in (0, 1):
+        w = W.random_small(30, 22, seed=5)
+        w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, fs_form=form))
+        s = oracle.Sim.from_workload(w)
+        s.step(9)
+        phi, mu = s.moments()["phi"], s.field(oracle.MU)
+        if form:
+            gx, gy = grad(phi)
+            ex, ey = mu * gx, mu * gy
+        else:
+            gx, gy = grad(mu)
+            ex, ey = -phi * gx, -phi * gy
+        np.testing.assert_allclose(s.field(oracle.FSX), ex, atol=1e-15)
+        np.testing.assert_allclose(s.field(oracle.FSY), ey, atol=1e-15)
 
 
 @pytest.mark.parametrize("ch", [1, 0])

@@ -81,6 +81,16 @@ def test_conservative_cahn_hilliard_form(lbm, bcy):
     assert_parity(got, ref, w)
 
 
+@pytest.mark.parametrize("bcy", [W.PERIODIC, W.WALL])
+def test_surface_force_mu_grad_phi(lbm, bcy):
+    """fs_form = 1 (F_s = mu grad phi) against the oracle in the same form."""
+    import dataclasses
+    w = W.random_small(58, 41, seed=19, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, fs_form=1))
+    _, got, ref = run_both(lbm, w, 200)
+    assert_parity(got, ref, w)
+
+
 def test_initial_state_moments(lbm):
     """t = 0: the moments of the initial populations (init kernel) match the oracle's."""
     w = W.random_small(45, 38, seed=9, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)

@@ -61,6 +61,7 @@ class Physical:
     bc_y: int = PERIODIC
     remove_Fa: int = 0      # 0: scheme as first stated, 1: additional interfacial force removed
     ch_conservative: int = 0  # 0: convective Cahn-Hilliard equation (as printed), 1: conservative form
+    fs_form: int = 0        # 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi)
 
 
 @dataclasses.dataclass
