@@ -82,11 +82,20 @@ extern "C" {
  *                 1: no source, the conservative form d_t phi + div(phi u) = ... (the f
  *                 collision conserves phi locally).
  *   fs_form       0 (default): surface-tension force F_s = -phi grad(mu) (the solved p is the
- *                 modified pressure p_h - phi mu); 1: F_s = mu grad(phi) (p is p_h). */
+ *                 modified pressure p_h - phi mu); 1: F_s = mu grad(phi) (p is p_h).
+ *   s_form        mass defect s = d_t rho + div(rho u) used with remove_Fa:
+ *                 0 (default): Eq. 5, s = rho' theta_M lap(mu);
+ *                 1: directly from the previous step, s^t = (rho^t - rho^{t-1}) +
+ *                    div(rho u)^{t-1} (isotropic divergence); the simulation then keeps rho and
+ *                    div(rho u) in two more planes per state buffer (8 B per cell each,
+ *                    lbm_sim_device_bytes counts them; at t = 0 the initial fields stand for
+ *                    t = -1).
+ *   pad           set to 0. */
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
     int ch_conservative, fs_form;
+    int s_form, pad;
 } lbm_params;
 
 /* FP64 diagnostics of the current state (reductions in a fixed order: bitwise reproducible).
@@ -118,6 +127,9 @@ LBM_API double lbm_tau_from_nu(double nu);
 /* Device bytes one simulation of nx x ny holds (both population buffers, field scratch and
  * reduction scratch) for the given storage. */
 LBM_API size_t lbm_device_bytes(int nx, int ny, int storage);
+
+/* Device bytes held by an existing simulation (lbm_device_bytes plus the s_form = 1 planes). */
+LBM_API size_t lbm_sim_device_bytes(const lbm_sim* sim);
 
 /* Create a simulation on the current CUDA device.  nx, ny >= 3 (>= 4 along a walled axis);
  * parameters are validated (tau > 1/2, densities, beta, kappa, phi* > 0, theta_M >= 0).

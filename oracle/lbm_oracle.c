@@ -15,7 +15,10 @@
  *   rho   = rho_B + c (rho_A - rho_B),  c = (phi + phi*) / (2 phi*)  clamped to [0,1] (Eq. 4)
  *   grad, lap: isotropic central differences over the D2Q9 neighbours            (experiments)
  *   F_s   = -phi grad(mu) (fs_form 0) or mu grad(phi) (fs_form 1),  G = (0, -rho g)  (Eq. 3)
- *   s     = rho' theta_M lap(mu)   = d_t rho + div(rho u) by Eq. 5
+ *   s     = rho' theta_M lap(mu)   = d_t rho + div(rho u) by Eq. 5              (s_form 0)
+ *         = (rho^t - rho^{t-1}) + div(rho u)^{t-1}, the mass defect taken directly from the
+ *           stored density and flux of the previous step (s_form 1; at t = 0 the initial
+ *           fields stand for t-1)
  *   u     = (sum_a e_a gbar_a / cs2 + (F_s + G)/2) / (rho - s/2 [corrected])
  *   p     = sum_a gbar_a + cs2 u.grad(rho) / 2
  *   grad(psi) = grad(p) - cs2 grad(rho),  psi = p - rho cs2                        (Eq. 6-8)
@@ -63,6 +66,8 @@ typedef struct {
     int bc_x, bc_y, remove_Fa, storage;
     int ch_conservative;    /* 0: convective Cahn-Hilliard (Eq. 2), 1: conservative form */
     int fs_form;            /* 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi) */
+    int s_form;             /* 0: s by Eq. 5, 1: s from the stored rho and div(rho u) */
+    int pad;
 } orc_params;
 
 typedef struct {
@@ -82,6 +87,7 @@ typedef struct {
     double *phi, *mu, *lap, *rho, *gpx, *gpy, *gmx, *gmy, *lmu;
     double *fsx, *fsy, *gy, *s, *ux, *uy, *p, *dpx, *dpy;
     double *divu, *w1, *w2;  /* div(u) and gradient scratch */
+    double *rho_prev, *D_prev, *rux, *ruy;  /* s_form 1: rho and div(rho u) of the last step */
 } orc_sim;
 
 static int opposite(int a) {
@@ -235,7 +241,7 @@ void lbm_destroy_ref(orc_sim* s) {
     double** fields[] = {&s->f, &s->g, &s->fs, &s->gs, &s->phi, &s->mu, &s->lap, &s->rho,
                          &s->gpx, &s->gpy, &s->gmx, &s->gmy, &s->lmu, &s->fsx, &s->fsy,
                          &s->gy, &s->s, &s->ux, &s->uy, &s->p, &s->dpx, &s->dpy,
-                         &s->divu, &s->w1, &s->w2};
+                         &s->divu, &s->w1, &s->w2, &s->rho_prev, &s->D_prev, &s->rux, &s->ruy};
     for (size_t i = 0; i < sizeof(fields) / sizeof(fields[0]); ++i) free(*fields[i]);
     free(s);
 }
@@ -262,7 +268,8 @@ int lbm_create_ref(int nx, int ny, const orc_params* P, orc_sim** out) {
     s->gs = alloc_field(Q * N);
     double** fields[] = {&s->phi, &s->mu, &s->lap, &s->rho, &s->gpx, &s->gpy, &s->gmx, &s->gmy,
                          &s->lmu, &s->fsx, &s->fsy, &s->gy, &s->s, &s->ux, &s->uy, &s->p,
-                         &s->dpx, &s->dpy, &s->divu, &s->w1, &s->w2};
+                         &s->dpx, &s->dpy, &s->divu, &s->w1, &s->w2, &s->rho_prev, &s->D_prev,
+                         &s->rux, &s->ruy};
     int ok = s->f && s->g && s->fs && s->gs;
     for (size_t i = 0; i < sizeof(fields) / sizeof(fields[0]); ++i) {
         *fields[i] = alloc_field(N);
@@ -289,6 +296,8 @@ static void chemical_potential(orc_sim* s) {
     }
 }
 
+static void store_mass_flux(orc_sim* s);
+
 int lbm_init_fields_ref(orc_sim* s, const double* phi0, const double* ux0, const double* uy0,
                         const double* p0) {
     if (!s || !phi0) return -1;
@@ -305,7 +314,11 @@ int lbm_init_fields_ref(orc_sim* s, const double* phi0, const double* ux0, const
             s->f[a * N + i] = feq[a];
             s->g[a * N + i] = geq[a];
         }
+        s->rho[i] = density(P, s->phi[i]);
+        s->ux[i] = ux;
+        s->uy[i] = uy;
     }
+    store_mass_flux(s);   /* the initial fields stand for the step before the first */
     s->step = 0;
     return 0;
 }
@@ -340,7 +353,7 @@ static void compute_moments(orc_sim* s) {
             s->fsy[i] = -ph * s->gmy[i];
         }
         s->gy[i] = -rho * P->gravity;
-        s->s[i] = rp * P->theta_M * s->lmu[i];
+        s->s[i] = P->s_form ? (rho - s->rho_prev[i]) + s->D_prev[i] : rp * P->theta_M * s->lmu[i];
         double jx = 0.0, jy = 0.0, m0 = 0.0;
         for (int a = 0; a < Q; ++a) {
             double gv = s->g[a * N + i];
@@ -354,6 +367,22 @@ static void compute_moments(orc_sim* s) {
         s->ux[i] = ux;
         s->uy[i] = uy;
         s->p[i] = m0 + 0.5 * CS2 * (ux * rp * s->gpx[i] + uy * rp * s->gpy[i]);
+    }
+}
+
+/* rho_prev = rho, D_prev = div(rho u) (isotropic) of the current moments. */
+static void store_mass_flux(orc_sim* s) {
+    const orc_params* P = &s->P;
+    size_t N = (size_t)s->nx * s->ny;
+    for (size_t i = 0; i < N; ++i) {
+        s->rux[i] = s->rho[i] * s->ux[i];
+        s->ruy[i] = s->rho[i] * s->uy[i];
+    }
+    orc_grad_iso(s->nx, s->ny, P->bc_x, P->bc_y, s->rux, s->D_prev, s->w1);
+    orc_grad_iso(s->nx, s->ny, P->bc_x, P->bc_y, s->ruy, s->w1, s->w2);
+    for (size_t i = 0; i < N; ++i) {
+        s->D_prev[i] += s->w2[i];
+        s->rho_prev[i] = s->rho[i];
     }
 }
 
@@ -429,6 +458,7 @@ int lbm_step_ref(orc_sim* s, int n) {
     if (!s || n < 0) return -1;
     for (int k = 0; k < n; ++k) {
         collide(s);
+        if (s->P.s_form) store_mass_flux(s);
         orc_stream(s->nx, s->ny, s->P.bc_x, s->P.bc_y, s->fs, s->f);
         orc_stream(s->nx, s->ny, s->P.bc_x, s->P.bc_y, s->gs, s->g);
         s->step++;

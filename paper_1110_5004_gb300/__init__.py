@@ -66,7 +66,7 @@ def params_from_physical(phys, storage=LBM_FP32) -> lbm_params:
                       tau_g_B=lib().lbm_tau_from_nu(phys.nu_B), rho_A=phys.rho_A,
                       rho_B=phys.rho_B, gravity=phys.gravity, bc_x=phys.bc_x, bc_y=phys.bc_y,
                       remove_Fa=phys.remove_Fa, storage=storage,
-                      ch_conservative=phys.ch_conservative, fs_form=phys.fs_form)
+                      ch_conservative=phys.ch_conservative, fs_form=phys.fs_form, s_form=phys.s_form)
 
 
 def device_bytes(nx, ny, storage=LBM_FP32) -> int:
@@ -127,6 +127,10 @@ class Sim:
     @property
     def launch_count(self):
         return int(lib().lbm_launch_count(self._h))
+
+    @property
+    def device_bytes(self):
+        return int(lib().lbm_sim_device_bytes(self._h))
 
     @property
     def checkpoint_bytes(self):

@@ -24,14 +24,14 @@ EXPORTS = (
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
     "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
-    "lbm_checkpoint", "lbm_restore",
+    "lbm_checkpoint", "lbm_restore", "lbm_sim_device_bytes",
 )
 
 
 class lbm_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "beta", "kappa", "phi_star", "theta_M", "tau_f", "tau_g_A", "tau_g_B", "rho_A", "rho_B",
-        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form")]
+        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form", "s_form", "pad")]
 
 
 class lbm_diag(ctypes.Structure):
@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "lbm_destroy": (ip, [vp]),
         "lbm_step_count": (ctypes.c_longlong, [vp]),
         "lbm_checkpoint_bytes": (ctypes.c_size_t, [vp]),
+        "lbm_sim_device_bytes": (ctypes.c_size_t, [vp]),
         "lbm_checkpoint": (ip, [vp, vp, ctypes.c_size_t]),
         "lbm_restore": (ip, [vp, vp, ctypes.c_size_t]),
         "lbm_set_stream": (ip, [vp, vp]),

@@ -48,6 +48,7 @@ Phys make_phys(const lbm_params& p) {
   P.remove_Fa = p.remove_Fa ? 1 : 0;
   P.ch_conv = p.ch_conservative ? 0 : 1;
   P.fs_mu = p.fs_form ? 1 : 0;
+  P.s_direct = p.s_form ? 1 : 0;
   P.kappa6 = (float)(p.kappa / 6.0);
   P.rho_prime12 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) / 12.0);
   P.s_coef6 = (float)((p.rho_A - p.rho_B) / (2.0 * p.phi_star) * p.theta_M / 6.0);
@@ -87,6 +88,7 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
   g.bc_x = s->params.bc_x;
   g.bc_y = s->params.bc_y;
   tile_geometry(s->nx, s->ny, s->nt, s->seg_h, s->sms * (s->occ > 0 ? s->occ : 1), &g.tile_w, &g.n_strips, &g.seg_h);
+  g.spoff = s->params.s_form ? (long long)s->pop_bytes : 0;
   return g;
 }
 
@@ -121,6 +123,7 @@ static int check_params(int nx, int ny, const lbm_params* p) {
   if (p->ch_conservative != 0 && p->ch_conservative != 1)
     return set_error("ch_conservative must be 0 or 1"), LBM_ERR_INVALID_ARG;
   if (p->fs_form != 0 && p->fs_form != 1) return set_error("fs_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
+  if (p->s_form != 0 && p->s_form != 1) return set_error("s_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 
@@ -148,6 +151,11 @@ size_t lbm_device_bytes(int nx, int ny, int storage) {
          ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double);
 }
 
+size_t lbm_sim_device_bytes(const lbm_sim* s) {
+  if (!s) return 0;
+  return lbm_device_bytes(s->nx, s->ny, s->params.storage) + 2 * (s->buf_bytes - s->pop_bytes);
+}
+
 int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out) {
   if (!out) return set_error("out is NULL"), LBM_ERR_INVALID_ARG;
   *out = nullptr;
@@ -163,6 +171,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
   s->phys = make_phys(*params);
   s->stream = (cudaStream_t)cuda_stream;
   const size_t pop_bytes = (size_t)state_bytes_per_cell(params->storage) * s->plane;
+  s->pop_bytes = pop_bytes;
+  s->buf_bytes = pop_bytes + (params->s_form ? 2 * sizeof(float) * (size_t)s->plane : 0);
   // FP16 keeps the O(mu, u) populations in its normal range: 2^12 maps 1.5e-8 .. 16 onto it
   if (params->storage == LBM_FP16_DEV) s->sf = s->sg = 4096.0f;
   cudaError_t e;
@@ -174,8 +184,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
     return rc;
   }
   s->occ = tile_occupancy(s->nt);
-  if ((e = cudaMalloc(&s->buf[0], pop_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&s->buf[1], pop_bytes)) != cudaSuccess ||
+  if ((e = cudaMalloc(&s->buf[0], s->buf_bytes)) != cudaSuccess ||
+      (e = cudaMalloc(&s->buf[1], s->buf_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&s->fields, (size_t)N_FIELDS * s->plane * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->red, ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double))) != cudaSuccess ||
       (e = cudaMallocHost(&s->h_diag, sizeof(lbm_diag))) != cudaSuccess) {
@@ -184,8 +194,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
     return rc;
   }
   // zero the pad columns once so no uninitialised memory is ever read back
-  cudaMemsetAsync(s->buf[0], 0, pop_bytes, s->stream);
-  cudaMemsetAsync(s->buf[1], 0, pop_bytes, s->stream);
+  cudaMemsetAsync(s->buf[0], 0, s->buf_bytes, s->stream);
+  cudaMemsetAsync(s->buf[1], 0, s->buf_bytes, s->stream);
   cudaMemsetAsync(s->fields, 0, (size_t)N_FIELDS * s->plane * sizeof(float), s->stream);
   if ((e = cudaGetLastError()) != cudaSuccess) {
     rc = cuda_fail(e, "lbm_create memset");
@@ -217,7 +227,7 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
     return rc;
   cudaError_t e = launch_init(s, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields launch");
-  s->launches += 2;
+  s->launches += s->params.s_form ? 3 : 2;
   s->steps = 0;
   // host inputs must be consumed before return (pageable copies already are; pinned ones not)
   if (!is_device_ptr(phi0) && (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
@@ -313,7 +323,7 @@ struct CkptHeader {
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 constexpr uint32_t CKPT_MAGIC = 0x434d424cu;   // "LBMC" little-endian
 
-size_t payload_bytes(const lbm_sim* s) { return (size_t)state_bytes_per_cell(s->params.storage) * s->plane; }
+size_t payload_bytes(const lbm_sim* s) { return s->buf_bytes; }
 }  // namespace
 
 extern "C" {

@@ -180,7 +180,7 @@ int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch** out) {
 int lbm_batch_add(lbm_batch* b, lbm_sim* s, int* slot) {
   if (!b || !s) return set_error("batch and sim are required"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation already belongs to a batch"), LBM_ERR_INVALID_ARG;
-  const size_t need = lbm_device_bytes(s->nx, s->ny, s->params.storage);
+  const size_t need = lbm_sim_device_bytes(s);
   if (b->budget && b->bytes + need > b->budget) {
     set_error("batch budget: %zu + %zu > %zu bytes", b->bytes, need, b->budget);
     return LBM_ERR_BUDGET;
@@ -212,7 +212,7 @@ int lbm_batch_remove(lbm_batch* b, int slot) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return cuda_fail(e, "batch remove sync");
   s->batch = nullptr;
-  b->bytes -= lbm_device_bytes(s->nx, s->ny, s->params.storage);
+  b->bytes -= lbm_sim_device_bytes(s);
   b->slots[slot] = nullptr;
   b->dirty = true;
   return LBM_OK;

@@ -78,6 +78,7 @@ struct Phys {
   float of3gf;          // omega_f 3 Gamma_f
   int ch_conv;          // 1: the f collision adds w_a phi div(u) (convective Cahn-Hilliard form)
   int fs_mu;            // 1: F_s = mu grad(phi); 0: F_s = -phi grad(mu)
+  int s_direct;         // 1: s = (rho - rho_prev) + div(rho u)_prev from the state's extra planes
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
@@ -104,6 +105,7 @@ struct Grid {
   int tile_w;           // interior columns per strip
   int seg_h;            // rows per segment
   int n_strips;
+  long long spoff;      // s_form 1: byte offset of the [rho, div(rho u)] planes in src/dst (else 0)
 };
 
 // Output planes of the moments mode (row-major with `pitch`).
@@ -563,10 +565,17 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
         const float gy = fmul(-P.gravity, rho);
         float sdef = 0.0f;
+        // cell index of row r (periodic halo rows wrap)
+        const int ci = (IN ? r : wrap1(r, g.ny)) * g.pitch + xp;
         if (P.remove_Fa) {
-          const float lmu6 = fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
-                                                     fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
-          sdef = fmul(P.s_coef6, lmu6);
+          if (P.s_direct) {
+            const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
+            sdef = fadd(fsub(rho, __ldg(sp + ci)), __ldg(sp + g.plane + ci));
+          } else {
+            const float lmu6 = fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
+                                                       fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
+            sdef = fmul(P.s_coef6, lmu6);
+          }
         }
         const float* gb = gp;
         const float s13 = fadd(gb[1], gb[3]), d13 = fsub(gb[1], gb[3]);
@@ -583,7 +592,9 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const float rx = fmul(P.rho_prime12, gphx), ry = fmul(P.rho_prime12, gphy);   // grad rho
         const float p = fmad(fmad(ux, rx, fmul(uy, ry)), 1.0f / 6.0f, m0g);
         put(o4, r, R_P, p, CK{});
-        if (MODE == MODE_STEP && P.ch_conv) put_u(r, ux, uy, CK{});
+        if (MODE == MODE_STEP && (P.ch_conv | P.s_direct)) put_u(r, ux, uy, CK{});
+        if (MODE == MODE_STEP && P.s_direct && in_w0 && (IN || (r >= ya && r < yb)))
+          reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff)[ci] = rho;   // rho^t for the next step
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && (IN || (r >= ya && r < yb))) {
             const int o = r * g.pitch + xp;
@@ -646,6 +657,27 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
+        if (P.s_direct) {
+          // div(rho u) of this step, for the next step's mass defect; rho from the phi rings as in S2
+          const float* xs_ = uring + (IN ? uslot(a - 6) : uslot_ck(a - 6)) + t;
+          const float* x0_ = uring + uslot(a - 5) + t;
+          const float* xn_ = uring + (IN ? uslot(a - 4) : uslot_ck(a - 4)) + t;
+          auto rho_at = [&](int o, int dc) {
+            const float ph_ = fadd(ring[o + R_PHI_HI * NT + t + dc], ring[o + R_PHI_LO * NT + t + dc]);
+            return fmad(__saturatef(fmad(ph_, P.inv_2phistar, 0.5f)), P.drho, P.rho_B);
+          };
+          const float rE = rho_at(o5, 1), rW = rho_at(o5, -1), rN = rho_at(o4, 0), rS = rho_at(o6, 0);
+          const float rNE = rho_at(o4, 1), rNW = rho_at(o4, -1), rSE = rho_at(o6, 1), rSW = rho_at(o6, -1);
+          const float jxE = fmul(rE, x0_[1]), jxW = fmul(rW, x0_[-1]);
+          const float jxNE = fmul(rNE, xn_[1]), jxNW = fmul(rNW, xn_[-1]), jxSE = fmul(rSE, xs_[1]), jxSW = fmul(rSW, xs_[-1]);
+          const float jyN = fmul(rN, xn_[NT]), jyS = fmul(rS, xs_[NT]);
+          const float jyNE = fmul(rNE, xn_[NT + 1]), jyNW = fmul(rNW, xn_[NT - 1]);
+          const float jySE = fmul(rSE, xs_[NT + 1]), jySW = fmul(rSW, xs_[NT - 1]);
+          const float djx = fmad(4.0f, fsub(jxE, jxW), fsub(fsub(jxNE, jxSW), fsub(jxNW, jxSE)));
+          const float djy = fmad(4.0f, fsub(jyN, jyS), fadd(fsub(jyNE, jySW), fsub(jyNW, jySE)));
+          float* sp = reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff);
+          sp[g.plane + r * g.pitch + xp] = fmul(fadd(djx, djy), 1.0f / 12.0f);
+        }
         collide_store<ST>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], phiD,
                           f, gb, g, r * g.pitch + xp);
       }

@@ -13,7 +13,9 @@ struct lbm_sim {
   lbm_params params{};
   lbm::Phys phys{};
   cudaStream_t stream = nullptr;
-  void* buf[2] = {nullptr, nullptr};   // post-collision state, state_bytes_per_cell x plane each
+  void* buf[2] = {nullptr, nullptr};   // post-collision state, buf_bytes each
+  size_t buf_bytes = 0;                // populations (+ rho, div(rho u) planes with s_form = 1)
+  size_t pop_bytes = 0;                // populations only
   int cur = 0;                         // buffer holding the current state
   float* fields = nullptr;             // 6 planes: phi, rho, ux, uy, p, mu (moments and init)
   double* red = nullptr;               // reduction scratch: ny rows x 12 partials + final record

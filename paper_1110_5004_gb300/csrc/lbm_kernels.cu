@@ -163,6 +163,31 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   }
 }
 
+// s_form 1: rho and div(rho u) of the initial fields, which stand for the step before the first.
+__global__ void k_init_sdef(Phys P, Grid g, const float* __restrict__ fields) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= g.nx) return;
+  const float* phi = fields;
+  const float* ux = fields + 2 * g.plane;
+  const float* uy = fields + 3 * g.plane;
+  auto idx = [&](int dx, int dy) {
+    int xx = x + dx, yy = y + dy;
+    xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
+    yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
+    return (long long)yy * g.pitch + xx;
+  };
+  auto rho = [&](long long i) { return fmad(__saturatef(fmad(phi[i], P.inv_2phistar, 0.5f)), P.drho, P.rho_B); };
+  auto jx = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), ux[i]); };
+  auto jy = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), uy[i]); };
+  const float djx = fmad(4.0f, fsub(jx(1, 0), jx(-1, 0)), fsub(fsub(jx(1, 1), jx(-1, -1)), fsub(jx(-1, 1), jx(1, -1))));
+  const float djy = fmad(4.0f, fsub(jy(0, 1), jy(0, -1)), fadd(fsub(jy(1, 1), jy(-1, -1)), fsub(jy(-1, 1), jy(1, -1))));
+  float* sp = reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff);
+  const long long c = (long long)y * g.pitch + x;
+  sp[c] = rho(c);
+  sp[g.plane + c] = fmul(fadd(djx, djy), 1.0f / 12.0f);
+}
+
 cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
   Grid g = make_grid(s, nullptr, s->buf[s->cur]);
   dim3 blk(128), grd((s->nx + 127) / 128, s->ny);
@@ -173,6 +198,11 @@ cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
     case ST_FP16: k_init_pop<ST_FP16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
     case ST_BF16: k_init_pop<ST_BF16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
     default: k_init_pop<ST_FP32><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
+  }
+  if (s->params.s_form) {
+    cudaError_t e2 = cudaGetLastError();
+    if (e2 != cudaSuccess) return e2;
+    k_init_sdef<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
   }
   return cudaGetLastError();
 }

@@ -26,15 +26,19 @@ from . import Sim
 KEYS = ("spread_radius", "centroid_x", "centroid_y", "vel_y", "liquid_area", "sum_phi", "finite")
 
 
-def run_pair(make, steps, every, snapshot_steps=(), stream=None):
+def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
     """Advance make(remove_Fa=0) and make(remove_Fa=1) for `steps` steps; diagnostics every
-    `every` steps, density fields at `snapshot_steps`."""
+    `every` steps, density fields at `snapshot_steps`.  `variants` maps further names to
+    functions of the corrected workload (e.g. another definition of the mass defect)."""
     import torch
     stream = stream if stream is not None else torch.cuda.current_stream()
     out = {}
     t0 = time.perf_counter()
-    for name, rf in (("original", 0), ("corrected", 1)):
+    runs = [("original", 0, None), ("corrected", 1, None)] + [(k, 1, f) for k, f in (variants or {}).items()]
+    for name, rf, fn in runs:
         w = make(remove_Fa=rf)
+        if fn is not None:
+            w = fn(w)
         sim = Sim.from_workload(w, stream=stream)
         series = {k: [] for k in ("step",) + KEYS}
         snaps = {}
@@ -58,19 +62,26 @@ def run_pair(make, steps, every, snapshot_steps=(), stream=None):
     return out
 
 
-def difference(res, key="spread_radius"):
-    """corrected - original of one diagnostic at the common steps where both are finite."""
-    a, b = res["original"]["series"], res["corrected"]["series"]
+def difference(res, key="spread_radius", other="corrected"):
+    """other - original of one diagnostic at the common steps where both are finite."""
+    a, b = res["original"]["series"], res[other]["series"]
     n = min(len(a["step"]), len(b["step"]))
     while n > 1 and not (a["finite"][n - 1] and b["finite"][n - 1]):
         n -= 1
     return np.asarray(a["step"][:n]), np.asarray(b[key][:n]) - np.asarray(a[key][:n])
 
 
-def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None):
+def _direct_defect(w):
+    import dataclasses
+    return dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
+
+
+def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None, direct_defect=False):
+    """direct_defect: also run the corrected scheme with the mass defect taken directly from the
+    stored density and flux (s_form = 1) instead of Eq. 5, to see how F_a depends on it."""
     import workloads as W
     res = run_pair(lambda remove_Fa: W.paper_falling_droplet(steps=steps, remove_Fa=remove_Fa), steps, every,
-                   snapshot_steps, stream)
+                   snapshot_steps, stream, {"corrected_direct_s": _direct_defect} if direct_defect else None)
     t, dr = difference(res)
     _, dy = difference(res, "centroid_y")
     r0 = res["original"]["series"]["spread_radius"][0]
@@ -81,6 +92,11 @@ def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None):
                       "relative_to_initial_radius": float(dr[-1] / r0),
                       "centroid_y_difference_at_end": float(dy[-1]),
                       "onset_step_5pct_of_radius": onset,
+                      **({"direct_s_spread_radius_difference_at_end": float(difference(res, other="corrected_direct_s")[1][-1]),
+                          "direct_s_centroid_y_difference_at_end":
+                              float(difference(res, "centroid_y", other="corrected_direct_s")[1][-1]),
+                          "direct_s_diverged_at": res["corrected_direct_s"]["diverged_at"]}
+                         if "corrected_direct_s" in res else {}),
                       "paper": "4.1 l.u. at t = 1.9e4 (26 % of the initial radius); parting from t = 1e4"}
     return res
 
@@ -113,7 +129,7 @@ def main():
     ap.add_argument("--falling-steps", type=int, default=19000)
     ap.add_argument("--splash-steps", type=int, default=3000)
     args = ap.parse_args()
-    res = {"falling_drop": falling_drop(args.falling_steps),
+    res = {"falling_drop": falling_drop(args.falling_steps, direct_defect=True),
            "splash_Re48": splash(48.0, args.splash_steps),
            "splash_Re480": splash(480.0, args.splash_steps)}
     js = {k: _jsonable(v) for k, v in res.items()}

@@ -27,7 +27,13 @@ def mix():
         W.falling_droplet(nx=64, ny=200, R=12.0, yc=150.0, ratio=10.0, steps=0),
         W.random_small(29, 31, seed=4, bc_x=W.WALL, bc_y=W.WALL, remove_Fa=1),
         W.random_small(300, 70, seed=5, bc_y=W.WALL),
+        direct_defect(W.random_small(77, 52, seed=6, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)),
     ]
+
+
+def direct_defect(w):
+    import dataclasses
+    return dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
 
 
 def test_alone_equals_in_mix_bitwise(lbm):

@@ -407,6 +407,33 @@ def test_laplace_law(fs_form):
         assert dp == pytest.approx(sigma / R, rel=0.05)
 
 
+@pytest.mark.parametrize("bcy", [W.PERIODIC, W.WALL])
+def test_direct_mass_defect(bcy):
+    """s_form = 1: s^t = (rho^t - rho^{t-1}) + div(rho u)^{t-1}, from the stored density and mass
+    flux of the previous step (the initial fields standing for t = -1), against the test's own
+    evaluation from the moments of consecutive steps; with F_a kept (remove_Fa = 0) s is not used
+    and both definitions give bitwise the same run."""
+    w = W.random_small(28, 21, seed=13, bc_y=bcy, gravity=2e-5 if bcy == W.WALL else 0.0, remove_Fa=1)
+    w1 = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
+    s = oracle.Sim.from_workload(w1)
+    prev = {"rho": np.clip((w.phi0.astype(float) + 1) / 2, 0, 1) * (w.phys.rho_A - w.phys.rho_B) + w.phys.rho_B,
+            "ux": w.ux0.astype(float), "uy": w.uy0.astype(float)}
+    for k in range(6):
+        m = s.moments()
+        expect = (m["rho"] - prev["rho"]) + iso_div(prev["rho"] * prev["ux"], prev["rho"] * prev["uy"],
+                                                    w.phys.bc_x, w.phys.bc_y)
+        np.testing.assert_allclose(s.field(oracle.S), expect, atol=1e-14)
+        prev = m
+        s.step(1)
+    runs = []
+    for form in (0, 1):
+        wf = dataclasses.replace(w, phys=dataclasses.replace(w.phys, remove_Fa=0, s_form=form))
+        o = oracle.Sim.from_workload(wf)
+        o.step(30)
+        runs.append(o.get_state())
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+
+
 def test_surface_force_forms():
     """F_s = mu grad(phi) (fs_form = 1) and -phi grad(mu) (fs_form = 0), each against the
     product of the oracle's phi and mu with the test's own isotropic gradient."""

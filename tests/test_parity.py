@@ -91,6 +91,17 @@ def test_surface_force_mu_grad_phi(lbm, bcy):
     assert_parity(got, ref, w)
 
 
+@pytest.mark.parametrize("bcx,bcy", [(W.PERIODIC, W.PERIODIC), (W.PERIODIC, W.WALL), (W.WALL, W.WALL)])
+def test_direct_mass_defect(lbm, bcx, bcy):
+    """s_form = 1 (mass defect from the stored rho and div(rho u) of the previous step) with
+    the corrected scheme, against the oracle in the same form; several tiles and segments."""
+    import dataclasses
+    w = W.random_small(97, 43, seed=23, bc_x=bcx, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
+    _, got, ref = run_both(lbm, w, 200, tile=(64, 9))
+    assert_parity(got, ref, w)
+
+
 def test_initial_state_moments(lbm):
     """t = 0: the moments of the initial populations (init kernel) match the oracle's."""
     w = W.random_small(45, 38, seed=9, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)

@@ -267,10 +267,12 @@ def test_preempted_requests_end_bitwise_as_uninterrupted(lbm, monkeypatch):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("storage", [0, 1])
-def test_checkpoint_restore_bitwise(lbm, storage):
+@pytest.mark.parametrize("storage,s_form", [(0, 0), (1, 0), (0, 1)])
+def test_checkpoint_restore_bitwise(lbm, storage, s_form):
+    import dataclasses
     import torch
     w = W.random_small(83, 47, seed=21, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=s_form))
     a = lbm.Sim.from_workload(w, storage=storage)
     a.step(37)
     ck = a.checkpoint()
@@ -290,6 +292,7 @@ def test_checkpoint_restore_bitwise(lbm, storage):
     c.restore(dev)
     assert c.step_count == 78 and np.array_equal(c.moments()["phi"], ma["phi"])
     # mismatches are rejected and leave the state unchanged
+    assert a.device_bytes == lbm.device_bytes(w.nx, w.ny, storage) + (16 * 47 * 96 if s_form else 0)
     other = lbm.Sim.from_workload(W.random_small(84, 47, seed=21), storage=storage)
     before = other.moments()["phi"]
     with pytest.raises(lbm.LBMError):

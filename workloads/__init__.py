@@ -62,6 +62,7 @@ class Physical:
     remove_Fa: int = 0      # 0: scheme as first stated, 1: additional interfacial force removed
     ch_conservative: int = 0  # 0: convective Cahn-Hilliard equation (as printed), 1: conservative form
     fs_form: int = 0        # 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi)
+    s_form: int = 0         # mass defect s: 0 by Eq. 5, 1 from the stored rho and div(rho u)
 
 
 @dataclasses.dataclass
