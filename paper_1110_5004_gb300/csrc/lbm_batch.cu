@@ -22,7 +22,8 @@ struct SimDesc {
   int pad;
 };
 
-template <int NT>
+// ANY_SD: some member uses the direct mass defect; only then is that tile body compiled in.
+template <int NT, bool ANY_SD>
 __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
                                               int n_work, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -34,10 +35,19 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
     const bool odd = ((d.cur0 + parity) & 1) != 0;
     g.src = odd ? d.buf1 : d.buf0;
     g.dst = odd ? const_cast<void*>(d.buf0) : d.buf1;
-    switch (g.storage) {   // members may differ in storage; the branch is uniform per tile
-      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      default: run_tile<NT, MODE_STEP, ST_FP32>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+    // members may differ in storage and mass-defect form; the branches are uniform per tile
+    if (ANY_SD && d.P.s_direct) {
+      switch (g.storage) {
+        case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+        case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+        default: run_tile<NT, MODE_STEP, ST_FP32, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      }
+    } else {
+      switch (g.storage) {
+        case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+        case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+        default: run_tile<NT, MODE_STEP, ST_FP32, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      }
     }
     __syncthreads();  // shared rings are reused by the next tile
   }
@@ -47,12 +57,26 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
 
 using namespace lbm;
 
-static cudaError_t set_batch_attr(int nt) {
+template <bool SD>
+static cudaError_t set_batch_attr_sd(int nt) {
   switch (nt) {
-    case 64: return cudaFuncSetAttribute(k_batch<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<64>));
-    case 256: return cudaFuncSetAttribute(k_batch<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
-    default: return cudaFuncSetAttribute(k_batch<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<128>));
+    case 64: return cudaFuncSetAttribute(k_batch<64, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<64>));
+    case 256: return cudaFuncSetAttribute(k_batch<256, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
+    default: return cudaFuncSetAttribute(k_batch<128, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<128>));
   }
+}
+
+static cudaError_t set_batch_attr(int nt, bool sd) { return sd ? set_batch_attr_sd<true>(nt) : set_batch_attr_sd<false>(nt); }
+
+template <bool SD>
+static int batch_occupancy_sd(int nt) {
+  int occ = 0;
+  switch (nt) {
+    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<64, SD>, 64, sizeof(Smem<64>)); break;
+    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<256, SD>, 256, sizeof(Smem<256>)); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<128, SD>, 128, sizeof(Smem<128>)); break;
+  }
+  return occ;
 }
 
 struct lbm_batch {
@@ -70,6 +94,7 @@ struct lbm_batch {
   int n_work = 0;
   int grid = 0;
   int flip = 0;                        // parity offset of every member since the last rebuild
+  bool any_sd = false;                 // some member uses the direct mass defect
   std::map<int, cudaGraphExec_t> graphs;  // 2k + flip -> executable graph for the membership
 };
 
@@ -138,12 +163,10 @@ static int rebuild(lbm_batch* b) {
   int dev = 0, sms = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if ((e = set_batch_attr(b->nt)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
-  switch (b->nt) {
-    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<64>, 64, sizeof(Smem<64>)); break;
-    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<256>, 256, sizeof(Smem<256>)); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<128>, 128, sizeof(Smem<128>)); break;
-  }
+  b->any_sd = false;
+  for (const SimDesc& d : sims) b->any_sd |= d.P.s_direct != 0;
+  if ((e = set_batch_attr(b->nt, b->any_sd)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+  occ = b->any_sd ? batch_occupancy_sd<true>(b->nt) : batch_occupancy_sd<false>(b->nt);
   b->grid = std::max(1, std::min(b->n_work, sms * std::max(occ, 1)));
   b->flip = 0;
   drop_graphs(b);
@@ -151,12 +174,17 @@ static int rebuild(lbm_batch* b) {
   return LBM_OK;
 }
 
-static cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t st) {
+template <bool SD>
+static void launch_batch_sd(lbm_batch* b, int parity, cudaStream_t st) {
   switch (b->nt) {
-    case 64: k_batch<64><<<b->grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
-    case 256: k_batch<256><<<b->grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
-    default: k_batch<128><<<b->grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    case 64: k_batch<64, SD><<<b->grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    case 256: k_batch<256, SD><<<b->grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    default: k_batch<128, SD><<<b->grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
   }
+}
+
+static cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t st) {
+  if (b->any_sd) launch_batch_sd<true>(b, parity, st); else launch_batch_sd<false>(b, parity, st);
   return cudaGetLastError();
 }
 

@@ -386,7 +386,8 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
 // is remapped.  Only one ghost row/column is ever read because every stage runs on real cells
 // and the stencils have radius 1.
 // Inlined into both kernels; its arithmetic is fixed by the explicit intrinsics above.
-template <int NT, int MODE, int ST>
+// SD: the direct mass defect (s_form 1) is compiled in; kernels without it carry none of its code.
+template <int NT, int MODE, int ST, bool SD>
 __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
                                       Smem<NT>& sm) {
   const int t = threadIdx.x;
@@ -565,10 +566,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
         const float gy = fmul(-P.gravity, rho);
         float sdef = 0.0f;
-        // cell index of row r (periodic halo rows wrap)
-        const int ci = (IN ? r : wrap1(r, g.ny)) * g.pitch + xp;
+        // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
+        auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
         if (P.remove_Fa) {
-          if (P.s_direct) {
+          if (SD) {
+            const int ci = cell_of();
             const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
             sdef = fadd(fsub(rho, __ldg(sp + ci)), __ldg(sp + g.plane + ci));
           } else {
@@ -592,9 +594,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const float rx = fmul(P.rho_prime12, gphx), ry = fmul(P.rho_prime12, gphy);   // grad rho
         const float p = fmad(fmad(ux, rx, fmul(uy, ry)), 1.0f / 6.0f, m0g);
         put(o4, r, R_P, p, CK{});
-        if (MODE == MODE_STEP && (P.ch_conv | P.s_direct)) put_u(r, ux, uy, CK{});
-        if (MODE == MODE_STEP && P.s_direct && in_w0 && (IN || (r >= ya && r < yb)))
-          reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff)[ci] = rho;   // rho^t for the next step
+        if (MODE == MODE_STEP && (P.ch_conv || SD)) put_u(r, ux, uy, CK{});
+        if (MODE == MODE_STEP && SD) {
+          if (in_w0 && (IN || (r >= ya && r < yb)))
+            reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff)[cell_of()] = rho;   // rho^t for the next step
+        }
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && (IN || (r >= ya && r < yb))) {
             const int o = r * g.pitch + xp;
@@ -657,7 +661,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
-        if (P.s_direct) {
+        if (SD) {
           // div(rho u) of this step, for the next step's mass defect; rho from the phi rings as in S2
           const float* xs_ = uring + (IN ? uslot(a - 6) : uslot_ck(a - 6)) + t;
           const float* x0_ = uring + uslot(a - 5) + t;

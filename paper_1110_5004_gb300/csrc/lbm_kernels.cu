@@ -8,29 +8,34 @@ namespace lbm {
 
 // ------------------------------------------------------------------ fused step / moments
 
-template <int NT, int MODE, int ST>
+template <int NT, int MODE, int ST, bool SD>
 // 512 / NT resident CTAs per SM (16 warps): caps the registers at 128 per thread.
 __global__ void __launch_bounds__(NT, 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
   const int strip = blockIdx.x % g.n_strips;
   const int seg = blockIdx.x / g.n_strips;
-  run_tile<NT, MODE, ST>(P, g, mo, strip, seg, sm);
+  run_tile<NT, MODE, ST, SD>(P, g, mo, strip, seg, sm);
 }
 
 static int n_tiles(const Grid& g) { return g.n_strips * ((g.ny + g.seg_h - 1) / g.seg_h); }
 
-template <int NT, int MODE, int ST>
-static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
+template <int NT, int MODE, int ST, bool SD>
+static cudaError_t launch_sd(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
   static bool attr_set = false;   // one GPU per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(Smem<NT>));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_tiles<NT, MODE, ST><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
+  k_tiles<NT, MODE, ST, SD><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
   return cudaGetLastError();
+}
+
+template <int NT, int MODE, int ST>
+static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
+  return P.s_direct ? launch_sd<NT, MODE, ST, true>(P, g, mo, st) : launch_sd<NT, MODE, ST, false>(P, g, mo, st);
 }
 
 template <int MODE, int ST>
@@ -57,9 +62,9 @@ template <int NT>
 static int occupancy_nt() {
   int occ = 0;
   // the dynamic shared-memory size above 48 KB is only admitted once the attribute is set
-  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP, ST_FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP, ST_FP32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(Smem<NT>));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP, ST_FP32>, NT, sizeof(Smem<NT>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP, ST_FP32, false>, NT, sizeof(Smem<NT>));
   cudaGetLastError();
   return occ > 0 ? occ : 1;
 }
