@@ -180,9 +180,22 @@ def cpu_baseline(w, steps):
         s.step(n)
         done += n
     dt = time.perf_counter() - t0
-    return {"value": w.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the same oracle on one core, over a shorter sample
+    one_steps = max(1, steps // 16)
+    oracle.set_threads(1)
+    try:
+        s.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
+        t1 = time.perf_counter()
+        s.step(one_steps)
+        dt1 = time.perf_counter() - t1
+    finally:
+        oracle.set_threads(cores)
+    return {"value": w.cells * steps / dt / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
             "sample": "%d FP64 oracle steps of %s (%d cells), re-initialised every %d steps, %.1f s"
-                      % (steps, w.name, w.cells, REINIT_EVERY, dt)}
+                      % (steps, w.name, w.cells, REINIT_EVERY, dt),
+            "single_core_mlups": w.cells * one_steps / dt1 / 1e6,
+            "single_core_sample": "%d steps on one core, %.1f s" % (one_steps, dt1)}
 
 
 def batch_leg(args, lbm, torch):
