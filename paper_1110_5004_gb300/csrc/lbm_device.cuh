@@ -10,6 +10,8 @@
 //   float pair f_0 + f_0lo (plane 18) so that phi, and through it mu and the surface-tension
 //   force, carry ~2^-48 relative precision with FP32 arithmetic.  All other populations are
 //   O(mu, u) and need no such care.
+//   With the direct mass defect (s_form 1) each buffer also holds, after the populations, two
+//   FP32 planes [rho, div(rho u)] of the step that wrote it.
 //
 // The fused step kernel marches a CTA up a strip of columns.  One thread owns one column of the
 // strip plus a 3-column halo on each side, and per row iteration runs four skewed stages whose
@@ -17,12 +19,15 @@
 //   S0 row a    : phi = sum_a f_a                               (strip + 3 halo columns)
 //   S1 row a-2  : mu = theta'(phi) - kappa lap(phi)               (strip + 2)     [Eq. 1]
 //   S2 row a-4  : grad phi, grad mu, lap mu, rho, F_s, G, s, u, p (strip + 1)     [Eq. 4, 5, 8]
-//   S3 row a-5  : grad p, grad psi, equilibria, forcing, BGK collisions of f and gbar, stores
+//   S3 row a-5  : grad p, grad psi, div u (convective Cahn-Hilliard source), equilibria,
+//                 forcing, BGK collisions of f and gbar, stores
 // so every population is read from HBM once and every stencil works from shared memory.  The
 // gathers of the next row (f for S0, gbar for S2) are issued one iteration ahead so their
 // latency overlaps the current row's arithmetic; the populations S3 needs again wait in
 // thread-private shared-memory rings.  One __syncthreads per row orders S2 -> S3; the ring
-// sizes keep every other reader/writer pair on distinct rows.
+// sizes keep every other reader/writer pair on distinct rows.  The pipeline fill and drain and
+// the iterations that touch a boundary row run a checked body; interior iterations run one with
+// no row tests.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
