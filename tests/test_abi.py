@@ -71,6 +71,10 @@ def _params(**kw):
     (16, 16, {"theta_M": -0.1}, b"theta_M"),
     (16, 16, {"bc_x": 7}, b"bc_x"),
     (1 << 16, 1 << 16, {}, b"too large"),
+    (16, 16, {"storage": 3}, b"storage"),
+    (16, 16, {"ch_conservative": 2}, b"ch_conservative"),
+    (16, 16, {"fs_form": -1}, b"fs_form"),
+    (16, 16, {"s_form": 5}, b"s_form"),
 ])
 def test_invalid_arguments_rejected_on_host(L, nx, ny, kw, msg):
     h = ctypes.c_void_p()
@@ -85,6 +89,20 @@ def test_null_handles(L):
     assert L.lbm_step_count(None) == -1
     assert L.lbm_create(8, 8, None, None, None) == -1
     assert L.lbm_strerror(-4) == b"simulation diverged"
+    assert L.lbm_checkpoint_bytes(None) == 0 and L.lbm_sim_device_bytes(None) == 0
+    buf = (ctypes.c_ubyte * 64)()
+    assert L.lbm_checkpoint(None, buf, 64) == -1
+    assert L.lbm_restore(None, buf, 64) == -1
+
+
+def test_params_layout_zero_defaults():
+    """A zero-initialised lbm_params selects the paper's forms: convective Cahn-Hilliard
+    (ch_conservative = 0), F_s = -phi grad(mu) (fs_form = 0), mass defect by Eq. 5 (s_form = 0);
+    the struct is 10 doubles + 8 ints with no padding, as include/lbm.h declares it."""
+    from paper_1110_5004_gb300 import lbm_params
+    p = lbm_params()
+    assert (p.ch_conservative, p.fs_form, p.s_form, p.remove_Fa) == (0, 0, 0, 0)
+    assert ctypes.sizeof(lbm_params) == 10 * 8 + 8 * 4
 
 
 def test_device_bytes_accounting(L):
