@@ -131,6 +131,24 @@ def test_tile_shape_does_not_change_results(lbm, nx):
             assert np.array_equal(o[k], outs[0][k]), k
 
 
+@pytest.mark.parametrize("bcx", [W.PERIODIC, W.WALL])
+def test_top_wall_row_inside_segment_fill(lbm, bcx):
+    """Segments whose fifth row (first row + 4) is the top wall row: the wall's mirrored ghost
+    row shares a ring slot with the segment's first halo row.  On a 29-row walled grid, segment
+    heights 8 and 4 both start a segment at row 24; the results must equal the single-segment
+    run bitwise and the oracle within tolerance."""
+    w = W.random_small(75, 29, seed=41, bc_x=bcx, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    outs = []
+    for tile in ((64, 29), (64, 8), (128, 4), (64, 1)):
+        s = lbm.Sim.from_workload(w, tile=tile)
+        s.step(30)
+        outs.append(s.moments())
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
+    assert_parity(outs[0], oracle.run(w, steps=30).moments(), w)
+
+
 @pytest.mark.parametrize("nx,tile", [(3193, (64, 0)), (14521, (128, 0)), (131, (64, 9)), (250, (64, 9))])
 def test_strip_ending_short_of_a_side_wall(lbm, nx, tile):
     """Side walls with many strips, among them the widths whose second-to-last strip ends 3
