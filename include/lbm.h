@@ -150,6 +150,14 @@ LBM_API int lbm_step(lbm_sim* sim, int n);
  * row-major nx*ny float32 each, host or device.  Synchronises the stream. */
 LBM_API int lbm_moments(lbm_sim* sim, float* phi, float* rho, float* ux, float* uy, float* p);
 
+/* The additional interfacial force of the current state (Eq. 12: F_a = -u [d_t rho + div(rho u)],
+ * evaluated as -u s with u the state's velocity and s the mass defect by the simulation's s_form:
+ * Eq. 5's rho' theta_M lap(mu), or the direct form from the stored density and flux), whether or
+ * not the scheme removes it; the paper's Fig. 3 shows its y component.  fa_x, fa_y: row-major
+ * nx*ny float32, host or device, either may be NULL.  Synchronises the stream.  Errors:
+ * LBM_ERR_INVALID_ARG for a NULL sim, LBM_ERR_CUDA for launch or copy failures. */
+LBM_API int lbm_interfacial_force(lbm_sim* sim, float* fa_x, float* fa_y);
+
 /* FP64 diagnostics of the current state into *out (host).  Returns LBM_ERR_DIVERGED (and
  * fills *out, finite = 0) when the state is no longer finite.  Synchronises the stream. */
 LBM_API int lbm_diagnostics(lbm_sim* sim, lbm_diag* out);

@@ -25,7 +25,7 @@ PERIODIC = 0
 WALL = 1
 CS2 = 1.0 / 3.0
 
-MU, S, FSX, FSY, DPX, DPY, GRAD_PHI_X, GRAD_PHI_Y, LAP_MU, TAU_G, DIVU = range(11)
+MU, S, FSX, FSY, DPX, DPY, GRAD_PHI_X, GRAD_PHI_Y, LAP_MU, TAU_G, DIVU, FAX, FAY = range(13)
 
 
 class Params(ctypes.Structure):

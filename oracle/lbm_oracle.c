@@ -26,6 +26,8 @@
  *   g^eq_a = cs2 rho Gamma_a + psi w_a = w_a p + rho cs2 (Gamma_a - w_a)
  *   S_a   = (e_a - u).[ F Gamma_a - (Gamma_a - w_a) grad(psi) ],
  *           F = F_s + G (scheme as first stated) or F_s + G + u s (F_a removed)   (Eq. 8, Eq. 12)
+ *   F_a   = -u s, the additional interfacial force (Eq. 12), exported as a field whichever
+ *           scheme runs (orc_field ORC_FAX / ORC_FAY; u as above, s by s_form)
  *   gbar_a(x + e_a, t+1) = gbar_a - (gbar_a - g^eq_a)/tau_g + (1 - 1/(2 tau_g)) S_a
  *   f^eq_a (a != 0) = w_a [Gamma_f mu / cs2 + phi (e.u/cs2 + (e.u)^2/(2 cs2^2) - u^2/(2 cs2))],
  *   f^eq_0 = phi - sum_{a != 0} f^eq_a,  Gamma_f = theta_M / (tau_f - 1/2)   (recovers Eq. 2)
@@ -480,7 +482,8 @@ int lbm_moments_ref(orc_sim* s, double* phi, double* rho, double* ux, double* uy
 
 /* Named work fields of the current state (after lbm_moments_ref / a collision). */
 enum { ORC_MU = 0, ORC_S = 1, ORC_FSX = 2, ORC_FSY = 3, ORC_DPX = 4, ORC_DPY = 5,
-       ORC_GRAD_PHI_X = 6, ORC_GRAD_PHI_Y = 7, ORC_LAP_MU = 8, ORC_TAU_G = 9, ORC_DIVU = 10 };
+       ORC_GRAD_PHI_X = 6, ORC_GRAD_PHI_Y = 7, ORC_LAP_MU = 8, ORC_TAU_G = 9, ORC_DIVU = 10,
+       ORC_FAX = 11, ORC_FAY = 12 };
 
 int orc_field(orc_sim* s, int which, double* out) {
     if (!s || !out) return -1;
@@ -502,6 +505,12 @@ int orc_field(orc_sim* s, int which, double* out) {
         case ORC_DIVU: src = s->divu; break;
         case ORC_TAU_G:
             for (size_t i = 0; i < N; ++i) out[i] = tau_g_of(&s->P, s->phi[i]);
+            return 0;
+        case ORC_FAX:   /* the additional interfacial force F_a = -u s (Eq. 12), x and y */
+            for (size_t i = 0; i < N; ++i) out[i] = -s->ux[i] * s->s[i];
+            return 0;
+        case ORC_FAY:
+            for (size_t i = 0; i < N; ++i) out[i] = -s->uy[i] * s->s[i];
             return 0;
         default: return -1;
     }

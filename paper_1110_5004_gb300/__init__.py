@@ -158,6 +158,16 @@ class Sim:
         _lib.check(lib().lbm_moments(self._h, *[_ptr(out.get(k)) for k in names]))
         return out
 
+    def interfacial_force(self, out=None):
+        """The additional interfacial force F_a = -u s of the current state (Eq. 12), whether or
+        not the scheme removes it: fax, fay as (ny, nx) float32 host arrays (or into the given
+        dict of host arrays / device tensors)."""
+        names = ("fax", "fay")
+        if out is None:
+            out = {k: np.empty((self.ny, self.nx), np.float32) for k in names}
+        _lib.check(lib().lbm_interfacial_force(self._h, *[_ptr(out.get(k)) for k in names]))
+        return out
+
     def diagnostics(self, raise_on_divergence=False):
         d = lbm_diag()
         rc = lib().lbm_diagnostics(self._h, ctypes.byref(d))

@@ -20,7 +20,7 @@ LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_BUDGET, LBM_ERR_DIVERGED, LBM_ERR_TIME
 # Every function the C ABI (include/lbm.h) declares.
 EXPORTS = (
     "lbm_params_from_sigma_W", "lbm_tau_from_nu", "lbm_device_bytes", "lbm_create", "lbm_init_fields",
-    "lbm_step", "lbm_moments", "lbm_diagnostics", "lbm_destroy", "lbm_step_count", "lbm_set_stream",
+    "lbm_step", "lbm_moments", "lbm_interfacial_force", "lbm_diagnostics", "lbm_destroy", "lbm_step_count", "lbm_set_stream",
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
     "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
         "lbm_init_fields": (ip, [vp, fp, fp, fp, fp]),
         "lbm_step": (ip, [vp, ip]),
         "lbm_moments": (ip, [vp, fp, fp, fp, fp, fp]),
+        "lbm_interfacial_force": (ip, [vp, fp, fp]),
         "lbm_diagnostics": (ip, [vp, ctypes.POINTER(lbm_diag)]),
         "lbm_destroy": (ip, [vp]),
         "lbm_step_count": (ctypes.c_longlong, [vp]),

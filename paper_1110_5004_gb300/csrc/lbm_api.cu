@@ -259,21 +259,40 @@ static int compute_moments(lbm_sim* s) {
   return LBM_OK;
 }
 
-int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float* p) {
-  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
-  int rc = compute_moments(s);
-  if (rc) return rc;
-  float* outs[5] = {phi, rho, ux, uy, p};
-  for (int k = 0; k < 5; ++k) {
+// Copy fields planes 0..n-1 (pitched) into the caller's nx*ny outputs (null ones skipped), then
+// synchronise the stream.
+static int copy_out(lbm_sim* s, float* const* outs, int n, const char* what) {
+  for (int k = 0; k < n; ++k) {
     if (!outs[k]) continue;
     const cudaMemcpyKind kind = is_device_ptr(outs[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     cudaError_t e = cudaMemcpy2DAsync(outs[k], (size_t)s->nx * sizeof(float), s->fields + (long long)k * s->plane,
                                       (size_t)s->pitch * sizeof(float), (size_t)s->nx * sizeof(float), s->ny, kind,
                                       s->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "lbm_moments copy");
+    if (e != cudaSuccess) return cuda_fail(e, what);
   }
   cudaError_t e = cudaStreamSynchronize(s->stream);
-  return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_moments sync");
+  return e == cudaSuccess ? LBM_OK : cuda_fail(e, what);
+}
+
+int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float* p) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  int rc = compute_moments(s);
+  if (rc) return rc;
+  float* outs[5] = {phi, rho, ux, uy, p};
+  return copy_out(s, outs, 5, "lbm_moments copy");
+}
+
+int lbm_interfacial_force(lbm_sim* s, float* fa_x, float* fa_y) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  Grid g = make_grid(s, s->buf[s->cur], nullptr);
+  MomentOut mo{};
+  mo.fax = s->fields;
+  mo.fay = s->fields + s->plane;
+  cudaError_t e = launch_moments(s->phys, g, mo, s->nt, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_interfacial_force launch");
+  s->launches++;
+  float* outs[2] = {fa_x, fa_y};
+  return copy_out(s, outs, 2, "lbm_interfacial_force copy");
 }
 
 int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {

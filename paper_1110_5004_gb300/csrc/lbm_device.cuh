@@ -114,8 +114,11 @@ struct Grid {
 };
 
 // Output planes of the moments mode (row-major with `pitch`).
+// Outputs of the moment pass; each may be null.  fax, fay: the additional interfacial force
+// F_a = -u s of Eq. 12 (s by the simulation's s_form), evaluated whichever scheme runs.
 struct MomentOut {
   float *phi, *rho, *ux, *uy, *p;
+  float *fax, *fay;
 };
 
 __device__ __forceinline__ int wrap(int i, int n) {
@@ -573,7 +576,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         float sdef = 0.0f;
         // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
         auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
-        if (P.remove_Fa) {
+        if (P.remove_Fa || (MODE == MODE_MOMENTS && mo.fax)) {
           if (SD) {
             const int ci = cell_of();
             const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
@@ -607,11 +610,15 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         if (MODE == MODE_MOMENTS) {
           if (in_w0 && (IN || (r >= ya && r < yb))) {
             const int o = r * g.pitch + xp;
-            mo.phi[o] = ph;
-            mo.rho[o] = rho;
-            mo.ux[o] = ux;
-            mo.uy[o] = uy;
-            mo.p[o] = p;
+            if (mo.phi) mo.phi[o] = ph;
+            if (mo.rho) mo.rho[o] = rho;
+            if (mo.ux) mo.ux[o] = ux;
+            if (mo.uy) mo.uy[o] = uy;
+            if (mo.p) mo.p[o] = p;
+            if (mo.fax) {
+              mo.fax[o] = fmul(-ux, sdef);
+              mo.fay[o] = fmul(-uy, sdef);
+            }
           }
         } else {
           if (in_w0 && (IN || r >= ya)) {

@@ -7,9 +7,10 @@ lattice units apart at t = 1.9e4 (about a quarter of the initial radius).  Splas
 (300 x 150, We = 960, Re = 48 and 480): the schemes agree at Re = 48 and differ at Re = 480.
 
 Each run records the FP64 diagnostics (spread radius, liquid centroid and velocity, total phi)
-every `every` steps and, optionally, density fields for contour plots; a run that leaves the
-finite range stops there and reports the step (the scheme, not the kernel: the FP64 oracle
-diverges at the same step).
+and the largest |F_a,y| of the additional interfacial force F_a = -u s (Eq. 12, evaluated in
+both schemes) every `every` steps and, optionally, density and F_a,y fields (the paper's Fig. 3)
+at chosen steps; a run that leaves the finite range stops there and reports the step (the
+scheme, not the kernel: the FP64 oracle diverges at the same step).
 
   python -m paper_1110_5004_gb300.experiments [--out results.json] [--falling-steps 19000]
 """
@@ -27,9 +28,10 @@ KEYS = ("spread_radius", "centroid_x", "centroid_y", "vel_y", "liquid_area", "su
 
 
 def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
-    """Advance make(remove_Fa=0) and make(remove_Fa=1) for `steps` steps; diagnostics every
-    `every` steps, density fields at `snapshot_steps`.  `variants` maps further names to
-    functions of the corrected workload (e.g. another definition of the mass defect)."""
+    """Advance make(remove_Fa=0) and make(remove_Fa=1) for `steps` steps; diagnostics and the
+    largest |F_a,y| every `every` steps, density and F_a,y fields at `snapshot_steps`.
+    `variants` maps further names to functions of the corrected workload (e.g. another
+    definition of the mass defect)."""
     import torch
     stream = stream if stream is not None else torch.cuda.current_stream()
     out = {}
@@ -40,7 +42,7 @@ def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
         if fn is not None:
             w = fn(w)
         sim = Sim.from_workload(w, stream=stream)
-        series = {k: [] for k in ("step",) + KEYS}
+        series = {k: [] for k in ("step",) + KEYS + ("max_abs_fa_y",)}
         snaps = {}
         done = 0
         while True:
@@ -48,8 +50,10 @@ def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
             series["step"].append(done)
             for k in KEYS:
                 series[k].append(float(d[k]))
+            fa_y = sim.interfacial_force()["fay"]
+            series["max_abs_fa_y"].append(float(np.abs(fa_y).max()) if d["finite"] else float("nan"))
             if done in snapshot_steps:
-                snaps[done] = sim.moments()["rho"]
+                snaps[done] = {"rho": sim.moments()["rho"], "fa_y": fa_y}
             if done >= steps or not d["finite"]:
                 break
             n = min(every, steps - done)
@@ -106,8 +110,16 @@ def splash(Re, steps=3000, every=50, snapshot_steps=(), stream=None):
     res = run_pair(lambda remove_Fa: W.paper_splash(Re=Re, steps=steps, remove_Fa=remove_Fa), steps, every,
                    snapshot_steps, stream)
     t, dr = difference(res)
+    # Fig. 3 shows F_a,y of the original scheme at t* = 1.8; report it there, or at the last
+    # finite diagnostic before it
+    o = res["original"]["series"]
+    fig3 = int(round(1.8 * 60.0 / 0.04))
+    idx = [i for i, (st, ok) in enumerate(zip(o["step"], o["finite"])) if ok and st <= fig3]
     res["summary"] = {"diverged_at": {k: res[k]["diverged_at"] for k in ("original", "corrected")},
                       "Re": Re, "t_star_per_step": 0.04 / 60.0,
+                      "fig3_step": fig3,
+                      "max_abs_fa_y_original": {"step": o["step"][idx[-1]], "value": o["max_abs_fa_y"][idx[-1]]}
+                      if idx else None,
                       "max_abs_spread_radius_difference": float(np.max(np.abs(dr))),
                       "spread_radius_difference_at_end": float(dr[-1])}
     return res

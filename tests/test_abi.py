@@ -93,6 +93,7 @@ def test_null_handles(L):
     buf = (ctypes.c_ubyte * 64)()
     assert L.lbm_checkpoint(None, buf, 64) == -1
     assert L.lbm_restore(None, buf, 64) == -1
+    assert L.lbm_interfacial_force(None, None, None) == -1 and L.lbm_moments(None, None, None, None, None, None) == -1
 
 
 def test_params_layout_zero_defaults():

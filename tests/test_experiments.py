@@ -54,8 +54,17 @@ def test_paper_falling_drop_gpu_matches_oracle(lbm, rf):
 
 def test_experiment_runner_reports_both_schemes(lbm):
     from paper_1110_5004_gb300 import experiments
-    res = experiments.falling_drop(steps=600, every=200)
+    res = experiments.falling_drop(steps=600, every=200, snapshot_steps=(400,))
     s = res["summary"]
+    # F_a = -u s (Eq. 12) is recorded in both schemes, as a series and as a field
+    for k in ("original", "corrected"):
+        fa = res[k]["series"]["max_abs_fa_y"]
+        assert len(fa) == 4 and all(v > 0.0 for v in fa[1:])
+        snap = res[k]["snapshots"][400]
+        assert snap["fa_y"].shape == (450, 150) and snap["rho"].shape == (450, 150)
+        assert float(np.abs(snap["fa_y"]).max()) == fa[2]
+    sp = experiments.splash(480.0, steps=200, every=100)["summary"]
+    assert sp["fig3_step"] == 2700 and sp["max_abs_fa_y_original"]["step"] == 200
     assert s["initial_spread_radius"] == pytest.approx(16.0, abs=0.05)
     assert s["diverged_at"] == {"original": None, "corrected": None}
     # before the flow develops the two schemes differ only through u.s, far below a lattice unit

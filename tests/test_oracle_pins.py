@@ -434,6 +434,37 @@ def test_direct_mass_defect(bcy):
     assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
 
 
+@pytest.mark.parametrize("remove_fa", [0, 1])
+def test_interfacial_force_definition(remove_fa):
+    """Eq. 12: F_a = -u [d_t rho + div(rho u)].  With the direct mass defect the bracket is
+    (rho^t - rho^{t-1}) + div(rho u)^{t-1}, evaluated here from consecutive moments with the
+    test's own stencil and multiplied by -u of the same moments; the field must not depend on
+    whether the scheme removes F_a.  Under Eq. 5's s it vanishes away from the interface."""
+    w = W.random_small(26, 19, seed=15, bc_y=W.WALL, gravity=2e-5, remove_Fa=remove_fa)
+    w1 = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
+    s = oracle.Sim.from_workload(w1)
+    prev = {"rho": np.clip((w.phi0.astype(float) + 1) / 2, 0, 1) * (w.phys.rho_A - w.phys.rho_B) + w.phys.rho_B,
+            "ux": w.ux0.astype(float), "uy": w.uy0.astype(float)}
+    for k in range(5):
+        m = s.moments()
+        defect = (m["rho"] - prev["rho"]) + iso_div(prev["rho"] * prev["ux"], prev["rho"] * prev["uy"],
+                                                    w.phys.bc_x, w.phys.bc_y)
+        fax, fay = s.field(oracle.FAX), s.field(oracle.FAY)
+        np.testing.assert_allclose(fax, -m["ux"] * defect, atol=1e-15)
+        np.testing.assert_allclose(fay, -m["uy"] * defect, atol=1e-15)
+        if k:
+            assert np.abs(fay).max() > 0.0
+        prev = m
+        s.step(1)
+    # Eq. 5's s: a drop relaxing from its initial profile feels F_a only in its interface
+    d = W.static_droplet(nx=48, ny=48, R=10.0, W=4.0, sigma=0.01, ratio=10.0, remove_Fa=remove_fa)
+    o = oracle.Sim.from_workload(d)
+    o.step(40)
+    fay, phi = o.field(oracle.FAY), o.moments()["phi"]
+    assert np.abs(fay).max() > 0.0
+    assert np.abs(fay[np.abs(phi) > 0.999]).max() < 1e-2 * np.abs(fay).max()   # the tanh tail: 1 - phi^2 ~ 2e-3
+
+
 def test_surface_force_forms():
     """F_s = mu grad(phi) (fs_form = 1) and -phi grad(mu) (fs_form = 0), each against the
     product of the oracle's phi and mu with the test's own isotropic gradient."""

@@ -102,6 +102,29 @@ def test_direct_mass_defect(lbm, bcx, bcy):
     assert_parity(got, ref, w)
 
 
+@pytest.mark.parametrize("rf,sform,bcy", [(0, 0, W.WALL), (1, 0, W.PERIODIC), (0, 1, W.WALL), (1, 1, W.PERIODIC)])
+def test_interfacial_force_field(lbm, rf, sform, bcy):
+    """F_a = -u s (Eq. 12) of the GPU state against the oracle's, with F_a kept and removed and
+    with both mass-defect forms.  Bound: 1e-3 of max|F_a| for the FP32 stencils (s is a second
+    difference of mu, itself one of phi), plus, for the direct form, max|u| times 8 ulps of
+    rho_A: its rho^t - rho^{t-1} cancels down to the FP32 rounding of the stored densities."""
+    import dataclasses
+    w = W.random_small(67, 41, seed=27, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0, remove_Fa=rf)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=sform))
+    sim = lbm.Sim.from_workload(w, tile=(64, 9))
+    sim.step(100)
+    got, m = sim.interfacial_force(), sim.moments()
+    o = oracle.run(w, steps=100)
+    ref = {"fax": o.field(oracle.FAX), "fay": o.field(oracle.FAY)}
+    umax = float(np.max(np.hypot(m["ux"], m["uy"])))
+    for k in ("fax", "fay"):
+        scale = float(np.abs(ref[k]).max())
+        assert scale > 0.0
+        bound = 1e-3 * scale + (umax * 8 * 2.0 ** -24 * w.phys.rho_A if sform else 0.0)
+        err = float(np.abs(got[k] - ref[k]).max())
+        assert err <= bound, (k, err, bound, scale)
+
+
 def test_initial_state_moments(lbm):
     """t = 0: the moments of the initial populations (init kernel) match the oracle's."""
     w = W.random_small(45, 38, seed=9, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
