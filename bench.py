@@ -297,6 +297,43 @@ def other_grids(lbm, torch, peak):
     return out
 
 
+def storage16_leg(lbm, torch, w, peak, flush_l2, steps=48):
+    """c3 with 16-bit population storage (FP16 and BF16 deviations from the lattice weights, FP32
+    arithmetic), timed like the main line: autotuned tile, L2 flushed before every timed step,
+    re-initialised every REINIT_EVERY steps outside the timed region.  The roofline is taken
+    against 72 B per lattice update (half the FP32 minimum)."""
+    from paper_1110_5004_gb300 import autotune
+    stream = torch.cuda.current_stream()
+    dev0 = [torch.from_numpy(getattr(w, k)).cuda() for k in ("phi0", "ux0", "uy0", "p0")]
+    out = {}
+    for name, st in (("fp16", 1), ("bf16", 2)):
+        sim = lbm.Sim.from_workload(w, stream=stream, storage=st)
+        t_, r_, _ = autotune.tune_sim(sim, reps=3)
+        for i in range(2 * REINIT_EVERY):
+            if i % REINIT_EVERY == 0:
+                sim.init_fields(*dev0)
+            sim.step(1)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            if i % REINIT_EVERY == 0:
+                sim.init_fields(*dev0)
+            flush_l2(i)
+            ev[i][0].record(stream)
+            sim.step(1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        dt = sum(a.elapsed_time(b) for a, b in ev) * 1e-3 / steps
+        mlups = w.cells / dt / 1e6
+        out[name] = {"mlups": mlups, "us_per_step": dt * 1e6, "tile": [t_, r_],
+                     "bytes_per_lu_algorithmic": B_MIN_FP32 // 2,
+                     "hbm_frac_of_measured": (B_MIN_FP32 // 2) * mlups * 1e6 / (peak * 1e9)}
+        sim.close()
+    out["workload"] = w.name
+    out["l2"] = "flushed between timed steps, as the main line"
+    return out
+
+
 def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
@@ -434,8 +471,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(w, args.cpu_steps)
 
-    batch = serving = others = None
+    batch = serving = others = st16 = None
     if not args.quick:
+        st16 = storage16_leg(lbm, torch, w, peak, flush_l2)
         others = other_grids(lbm, torch, peak)
         import workloads as W
         batch = batch_leg(args, lbm, torch)
@@ -465,6 +503,7 @@ def run_ours(args):
                 "cpu_baseline": cpu,
                 "batch": batch,
                 "serving": serving,
+                "storage16": st16,
                 "other_grids": others}
         print(json.dumps(line), flush=True)
     if world > 1:
