@@ -225,11 +225,13 @@ def test_c2_falling_droplet_until_divergence(lbm):
     assert abs(first["gpu"] - first["ref"]) <= 2
 
 
-def test_c3_splash_until_divergence(lbm):
-    """c3 (2048x512, rho 1:0.001, Re 500, We 8000): parity over the first steps at full size;
+@pytest.mark.parametrize("tile", [None, (256, 16)])
+def test_c3_splash_until_divergence(lbm, tile):
+    """c3 (2048x512, rho 1:0.001, Re 500, We 8000): parity over the first steps at full size,
+    with the default tile and with the one the benchmark times on GB300 (256 threads x 16 rows);
     both sides diverge within the first dozen steps."""
     w = W.splash()
-    sim = lbm.Sim.from_workload(w)
+    sim = lbm.Sim.from_workload(w, tile=tile)
     ref = oracle.Sim.from_workload(w)
     sim.step(3)
     ref.step(3)
@@ -238,6 +240,20 @@ def test_c3_splash_until_divergence(lbm):
         sim.step(1)
         ref.step(1)
     assert not sim.diagnostics()["finite"] and not ref.diagnostics()["finite"]
+
+
+@pytest.mark.parametrize("name,st", [("fp16", 1), ("bf16", 2)])
+def test_c3_splash_16bit_storage(lbm, name, st):
+    """c3 at full size with 16-bit population storage (FP32 arithmetic) on the benchmark's tile:
+    phi within the reduced-storage bound of 1e-3 (FP16) of the FP64 oracle after 3 steps; BF16's
+    8-bit mantissa is held to 3e-2, as on the other grids."""
+    w = W.splash()
+    sim = lbm.Sim.from_workload(w, tile=(256, 16), storage=st)
+    sim.step(3)
+    ref = oracle.run(w, steps=3).moments()
+    got = sim.moments()
+    err = float(np.abs(got["phi"] - ref["phi"]).max() / np.abs(ref["phi"]).max())
+    assert err <= (1e-3 if st == 1 else 3e-2), (name, err)
 
 
 def test_diverged_state_reports_error_code(lbm):
