@@ -157,6 +157,7 @@ size_t lbm_sim_device_bytes(const lbm_sim* s) {
 }
 
 int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out) {
+  Range range_("lbm_create");
   if (!out) return set_error("out is NULL"), LBM_ERR_INVALID_ARG;
   *out = nullptr;
   int rc = check_params(nx, ny, params);
@@ -220,6 +221,7 @@ static int upload_field(lbm_sim* s, int k, const float* src) {
 }
 
 int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float* uy0, const float* p0) {
+  Range range_("lbm_init_fields");
   if (!s || !phi0) return set_error("sim and phi0 are required"), LBM_ERR_INVALID_ARG;
   int rc;
   if ((rc = upload_field(s, 0, phi0)) || (rc = upload_field(s, 2, ux0)) || (rc = upload_field(s, 3, uy0)) ||
@@ -236,6 +238,7 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
 }
 
 int lbm_step(lbm_sim* s, int n) {
+  Range range_("lbm_step");
   if (!s || n < 0) return set_error("invalid sim or step count"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation is a batch member; step it through its batch"), LBM_ERR_INVALID_ARG;
   for (int i = 0; i < n; ++i) {
@@ -275,6 +278,7 @@ static int copy_out(lbm_sim* s, float* const* outs, int n, const char* what) {
 }
 
 int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float* p) {
+  Range range_("lbm_moments");
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
   int rc = compute_moments(s);
   if (rc) return rc;
@@ -283,6 +287,7 @@ int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float*
 }
 
 int lbm_interfacial_force(lbm_sim* s, float* fa_x, float* fa_y) {
+  Range range_("lbm_interfacial_force");
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
   Grid g = make_grid(s, s->buf[s->cur], nullptr);
   MomentOut mo{};
@@ -296,6 +301,7 @@ int lbm_interfacial_force(lbm_sim* s, float* fa_x, float* fa_y) {
 }
 
 int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {
+  Range range_("lbm_diagnostics");
   if (!s || !out) return set_error("sim and out are required"), LBM_ERR_INVALID_ARG;
   int rc = compute_moments(s);
   if (rc) return rc;
@@ -350,6 +356,7 @@ extern "C" {
 size_t lbm_checkpoint_bytes(const lbm_sim* s) { return s ? sizeof(CkptHeader) + payload_bytes(s) : 0; }
 
 int lbm_checkpoint(lbm_sim* s, void* buf, size_t bytes) {
+  Range range_("lbm_checkpoint");
   if (!s || !buf) return set_error("sim and buf are required"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("remove the simulation from its batch before a checkpoint"), LBM_ERR_INVALID_ARG;
   if (bytes < lbm_checkpoint_bytes(s))
@@ -374,6 +381,7 @@ int lbm_checkpoint(lbm_sim* s, void* buf, size_t bytes) {
 }
 
 int lbm_restore(lbm_sim* s, const void* buf, size_t bytes) {
+  Range range_("lbm_restore");
   if (!s || !buf) return set_error("sim and buf are required"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("remove the simulation from its batch before a restore"), LBM_ERR_INVALID_ARG;
   if (bytes < sizeof(CkptHeader)) return set_error("checkpoint shorter than its header"), LBM_ERR_INVALID_ARG;

@@ -206,6 +206,7 @@ int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch** out) {
 }
 
 int lbm_batch_add(lbm_batch* b, lbm_sim* s, int* slot) {
+  Range range_("lbm_batch_add");
   if (!b || !s) return set_error("batch and sim are required"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation already belongs to a batch"), LBM_ERR_INVALID_ARG;
   const size_t need = lbm_sim_device_bytes(s);
@@ -234,6 +235,7 @@ int lbm_batch_add(lbm_batch* b, lbm_sim* s, int* slot) {
 }
 
 int lbm_batch_remove(lbm_batch* b, int slot) {
+  Range range_("lbm_batch_remove");
   if (!b || slot < 0 || slot >= (int)b->slots.size() || !b->slots[slot])
     return set_error("invalid batch slot %d", slot), LBM_ERR_INVALID_ARG;
   lbm_sim* s = b->slots[slot];
@@ -247,6 +249,7 @@ int lbm_batch_remove(lbm_batch* b, int slot) {
 }
 
 int lbm_batch_step(lbm_batch* b, int k) {
+  Range range_("lbm_batch_step");
   if (!b || k < 0) return set_error("invalid batch or step count"), LBM_ERR_INVALID_ARG;
   if (k == 0) return LBM_OK;
   int rc;

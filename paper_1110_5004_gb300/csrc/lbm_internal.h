@@ -4,6 +4,8 @@
 #include <stddef.h>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>  // header-only; a no-op unless a profiler is attached
+
 #include "lbm.h"  // include/ is on the include path
 #include "lbm_device.cuh"
 
@@ -31,6 +33,14 @@ struct lbm_sim {
 };
 
 namespace lbm {
+
+// Named range on the profiler's timeline for the duration of one entry point.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 constexpr int N_FIELDS = 6;
 constexpr int DIAG_PARTIALS = 12;
