@@ -465,6 +465,36 @@ def test_interfacial_force_definition(remove_fa):
     assert np.abs(fay[np.abs(phi) > 0.999]).max() < 1e-2 * np.abs(fay).max()   # the tanh tail: 1 - phi^2 ~ 2e-3
 
 
+def test_diagnostics_against_geometry():
+    """The FP64 diagnostics on a tanh drop of radius R and width W centred in a large periodic
+    box.  Its liquid fraction is a logistic step in r, so, to exponentially small terms:
+    liquid area pi (R^2 + pi^2 W^2 / 48) (the step's second moment), centroid at the centre,
+    spread radius R (the central chord of an even logistic step integrates to 2R), total phi
+    2 area - N.  With a uniform initial velocity U (and a negligible tension) the liquid-
+    weighted velocity is U and the largest speed |U|.  With u = 0 the reported p is the initial
+    p0, so a two-level p0 gives back its levels as the liquid and gas pressures."""
+    n, R, Wd = 128, 20.0, 4.0
+    base = W.static_droplet(nx=n, ny=n, R=R, W=Wd, sigma=1e-8, ratio=10.0)
+    U = (0.01, -0.02)
+    w = dataclasses.replace(base, ux0=np.full((n, n), U[0], np.float32), uy0=np.full((n, n), U[1], np.float32))
+    d = oracle.Sim.from_workload(w).diagnostics()
+    area = math.pi * (R * R + math.pi ** 2 * Wd ** 2 / 48.0)
+    assert d["liquid_area"] == pytest.approx(area, rel=1e-6)
+    assert d["centroid_x"] == pytest.approx(n / 2, abs=1e-9) and d["centroid_y"] == pytest.approx(n / 2, abs=1e-9)
+    assert d["spread_radius"] == pytest.approx(R, rel=1e-6)
+    assert d["sum_phi"] == pytest.approx(2 * area - n * n, rel=1e-6)
+    assert d["vel_x"] == pytest.approx(U[0], rel=1e-5) and d["vel_y"] == pytest.approx(U[1], rel=1e-5)
+    assert d["max_u"] == pytest.approx(math.hypot(*U), rel=1e-5)
+    assert d["finite"]
+    pl, pg = 2.0 ** -8, -(2.0 ** -9)          # exact in the float32 input
+    w = dataclasses.replace(base, p0=np.where(base.phi0 > 0, pl, pg).astype(np.float32))
+    d = oracle.Sim.from_workload(w).diagnostics()
+    assert d["p_liquid"] == pytest.approx(pl, rel=1e-9) and d["p_gas"] == pytest.approx(pg, rel=1e-9)
+    # a non-finite value anywhere is reported
+    w = dataclasses.replace(base, ux0=np.where(np.arange(n * n).reshape(n, n) == 77, np.nan, 0.0).astype(np.float32))
+    assert not oracle.Sim.from_workload(w).diagnostics()["finite"]
+
+
 def test_surface_force_forms():
     """F_s = mu grad(phi) (fs_form = 1) and -phi grad(mu) (fs_form = 0), each against the
     product of the oracle's phi and mu with the test's own isotropic gradient."""
