@@ -90,20 +90,21 @@ cudaError_t launch_moments(const Phys& P, const Grid& g, const MomentOut& mo, in
 
 __global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
   if (x >= g.nx) return;
-  const float* phi = fields;
-  float* mu = fields + 5 * (long long)g.plane;
-  auto at = [&](int dx, int dy) {
-    int xx = x + dx, yy = y + dy;
-    xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
-    yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
-    return phi[(long long)yy * g.pitch + xx];
-  };
-  const float ph = at(0, 0);
-  const float lap = (4.0f * (at(1, 0) + at(0, 1) + at(-1, 0) + at(0, -1)) +
-                     (at(1, 1) + at(-1, 1) + at(-1, -1) + at(1, -1)) - 20.0f * ph) * (1.0f / 6.0f);
-  mu[(long long)y * g.pitch + x] = P.four_beta * ph * (ph * ph - P.phi_star2) - P.kappa * lap;
+  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
+    const float* phi = fields;
+    float* mu = fields + 5 * (long long)g.plane;
+    auto at = [&](int dx, int dy) {
+      int xx = x + dx, yy = y + dy;
+      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
+      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
+      return phi[(long long)yy * g.pitch + xx];
+    };
+    const float ph = at(0, 0);
+    const float lap = (4.0f * (at(1, 0) + at(0, 1) + at(-1, 0) + at(0, -1)) +
+                       (at(1, 1) + at(-1, 1) + at(-1, -1) + at(1, -1)) - 20.0f * ph) * (1.0f / 6.0f);
+    mu[(long long)y * g.pitch + x] = P.four_beta * ph * (ph * ph - P.phi_star2) - P.kappa * lap;
+  }
 }
 
 // Post-collision-layout state whose pull gives f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0):
@@ -112,90 +113,92 @@ __global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
 template <int ST>
 __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
   if (x >= g.nx) return;
-  const float* phi = fields;
-  const float* ux = fields + 2 * g.plane;
-  const float* uy = fields + 3 * g.plane;
-  const float* pp = fields + 4 * g.plane;
-  const float* mu = fields + 5 * (long long)g.plane;
-  const long long cell = (long long)y * g.pitch + x;
-#pragma unroll
-  for (int a = 0; a < Q; ++a) {
-    int xw = x + cx(a), yw = y + cy(a);
-    int b = a;
-    bool hit = false;
-    if (xw < 0 || xw >= g.nx) {
-      if (g.bc_x == BC_WALL) hit = true; else xw = wrap(xw, g.nx);
-    }
-    if (yw < 0 || yw >= g.ny) {
-      if (g.bc_y == BC_WALL) hit = true; else yw = wrap(yw, g.ny);
-    }
-    if (hit) {
-      xw = x;
-      yw = y;
-      b = opp(a);
-    }
-    const long long c = (long long)yw * g.pitch + xw;
-    const float ph = phi[c], u = ux[c], v = uy[c], p = pp[c], m = mu[c];
-    const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
-    const float rho = P.rho_B + cl * P.drho;
-    const float uu15 = 1.5f * (u * u + v * v);
-    const float w = wgt(b);
-    const float eu = (float)cx(b) * u + (float)cy(b) * v;
-    const float poly = 3.0f * eu + 4.5f * eu * eu - uu15;
-    const float geq = w * p + rho * (1.0f / 3.0f) * (w * poly);
-    if (b == 0) {
-      // f_0^eq = phi - sum_{k>0} f^eq_k, kept as the float pair (hi, lo)
-      float rest = 0.0f;
-#pragma unroll
-      for (int k = 1; k < Q; ++k) {
-        const float ek = (float)cx(k) * u + (float)cy(k) * v;
-        rest += wgt(k) * (P.three_gamma_f * m + ph * (3.0f * ek + 4.5f * ek * ek - uu15));
+  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
+    const float* phi = fields;
+    const float* ux = fields + 2 * g.plane;
+    const float* uy = fields + 3 * g.plane;
+    const float* pp = fields + 4 * g.plane;
+    const float* mu = fields + 5 * (long long)g.plane;
+    const long long cell = (long long)y * g.pitch + x;
+  #pragma unroll
+    for (int a = 0; a < Q; ++a) {
+      int xw = x + cx(a), yw = y + cy(a);
+      int b = a;
+      bool hit = false;
+      if (xw < 0 || xw >= g.nx) {
+        if (g.bc_x == BC_WALL) hit = true; else xw = wrap(xw, g.nx);
       }
-      float hi, lo;
-      two_sum(ph, -rest, hi, lo);
-      if (ST == ST_FP32) {
-        st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi, 1.0f);
-        st_pop<ST>(g.dst, g.plane, PLANE_F0LO, (int)cell, lo, 1.0f);
+      if (yw < 0 || yw >= g.ny) {
+        if (g.bc_y == BC_WALL) hit = true; else yw = wrap(yw, g.ny);
+      }
+      if (hit) {
+        xw = x;
+        yw = y;
+        b = opp(a);
+      }
+      const long long c = (long long)yw * g.pitch + xw;
+      const float ph = phi[c], u = ux[c], v = uy[c], p = pp[c], m = mu[c];
+      const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
+      const float rho = P.rho_B + cl * P.drho;
+      const float uu15 = 1.5f * (u * u + v * v);
+      const float w = wgt(b);
+      const float eu = (float)cx(b) * u + (float)cy(b) * v;
+      const float poly = 3.0f * eu + 4.5f * eu * eu - uu15;
+      const float geq = w * p + rho * (1.0f / 3.0f) * (w * poly);
+      if (b == 0) {
+        // f_0^eq = phi - sum_{k>0} f^eq_k, kept as the float pair (hi, lo)
+        float rest = 0.0f;
+  #pragma unroll
+        for (int k = 1; k < Q; ++k) {
+          const float ek = (float)cx(k) * u + (float)cy(k) * v;
+          rest += wgt(k) * (P.three_gamma_f * m + ph * (3.0f * ek + 4.5f * ek * ek - uu15));
+        }
+        float hi, lo;
+        two_sum(ph, -rest, hi, lo);
+        if (ST == ST_FP32) {
+          st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi, 1.0f);
+          st_pop<ST>(g.dst, g.plane, PLANE_F0LO, (int)cell, lo, 1.0f);
+        } else {
+          st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi + lo, 1.0f);
+        }
       } else {
-        st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi + lo, 1.0f);
+        st_pop<ST>(g.dst, g.plane, a, (int)cell, w * (P.three_gamma_f * m + ph * poly), g.sf);
       }
-    } else {
-      st_pop<ST>(g.dst, g.plane, a, (int)cell, w * (P.three_gamma_f * m + ph * poly), g.sf);
+      st_pop<ST>(g.dst, g.plane, Q + a, (int)cell, geq, g.sg);
     }
-    st_pop<ST>(g.dst, g.plane, Q + a, (int)cell, geq, g.sg);
   }
 }
 
 // s_form 1: rho and div(rho u) of the initial fields, which stand for the step before the first.
 __global__ void k_init_sdef(Phys P, Grid g, const float* __restrict__ fields) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int y = blockIdx.y;
   if (x >= g.nx) return;
-  const float* phi = fields;
-  const float* ux = fields + 2 * g.plane;
-  const float* uy = fields + 3 * g.plane;
-  auto idx = [&](int dx, int dy) {
-    int xx = x + dx, yy = y + dy;
-    xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
-    yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
-    return (long long)yy * g.pitch + xx;
-  };
-  auto rho = [&](long long i) { return fmad(__saturatef(fmad(phi[i], P.inv_2phistar, 0.5f)), P.drho, P.rho_B); };
-  auto jx = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), ux[i]); };
-  auto jy = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), uy[i]); };
-  const float djx = fmad(4.0f, fsub(jx(1, 0), jx(-1, 0)), fsub(fsub(jx(1, 1), jx(-1, -1)), fsub(jx(-1, 1), jx(1, -1))));
-  const float djy = fmad(4.0f, fsub(jy(0, 1), jy(0, -1)), fadd(fsub(jy(1, 1), jy(-1, -1)), fsub(jy(-1, 1), jy(1, -1))));
-  float* sp = reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff);
-  const long long c = (long long)y * g.pitch + x;
-  sp[c] = rho(c);
-  sp[g.plane + c] = fmul(fadd(djx, djy), 1.0f / 12.0f);
+  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
+    const float* phi = fields;
+    const float* ux = fields + 2 * g.plane;
+    const float* uy = fields + 3 * g.plane;
+    auto idx = [&](int dx, int dy) {
+      int xx = x + dx, yy = y + dy;
+      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
+      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
+      return (long long)yy * g.pitch + xx;
+    };
+    auto rho = [&](long long i) { return fmad(__saturatef(fmad(phi[i], P.inv_2phistar, 0.5f)), P.drho, P.rho_B); };
+    auto jx = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), ux[i]); };
+    auto jy = [&](int dx, int dy) { const long long i = idx(dx, dy); return fmul(rho(i), uy[i]); };
+    const float djx = fmad(4.0f, fsub(jx(1, 0), jx(-1, 0)), fsub(fsub(jx(1, 1), jx(-1, -1)), fsub(jx(-1, 1), jx(1, -1))));
+    const float djy = fmad(4.0f, fsub(jy(0, 1), jy(0, -1)), fadd(fsub(jy(1, 1), jy(-1, -1)), fsub(jy(-1, 1), jy(1, -1))));
+    float* sp = reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff);
+    const long long c = (long long)y * g.pitch + x;
+    sp[c] = rho(c);
+    sp[g.plane + c] = fmul(fadd(djx, djy), 1.0f / 12.0f);
+  }
 }
 
 cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
   Grid g = make_grid(s, nullptr, s->buf[s->cur]);
-  dim3 blk(128), grd((s->nx + 127) / 128, s->ny);
+  dim3 blk(128), grd((s->nx + 127) / 128, s->ny < 65535 ? s->ny : 65535);
   k_init_mu<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -172,6 +172,16 @@ def test_top_wall_row_inside_segment_fill(lbm, bcx):
     assert_parity(outs[0], oracle.run(w, steps=30).moments(), w)
 
 
+def test_grid_taller_than_a_launch_dimension(lbm):
+    """70 000 rows, more than a grid's y dimension allows (65 535): initialisation, steps,
+    moments and the FP64 diagnostics against the oracle."""
+    w = W.random_small(24, 70000, seed=44, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    sim, got, ref = run_both(lbm, w, 3)
+    assert_parity(got, ref, w)
+    d = sim.diagnostics()
+    assert d["finite"] and abs(d["sum_phi"] - float(ref["phi"].sum())) <= 1e-6 * w.cells
+
+
 @pytest.mark.parametrize("nx,tile", [(3193, (64, 0)), (14521, (128, 0)), (131, (64, 9)), (250, (64, 9))])
 def test_strip_ending_short_of_a_side_wall(lbm, nx, tile):
     """Side walls with many strips, among them the widths whose second-to-last strip ends 3
