@@ -172,14 +172,22 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Population a (0..8 f, 9..17 gbar, 18 f_0lo) at element idx of its plane.
+// Population a (0..8 f, 9..17 gbar, 18 f_0lo) at element idx of its plane, as stored bits (a float,
+// or a 16-bit value in the low half), and their decoding.  A prefetch keeps the bits and decodes
+// them where they are used, so that the conversion does not wait for the load at the point of issue.
 template <int ST>
-__device__ __forceinline__ float ld_pop(const void* __restrict__ base, int plane, int a, int idx, float inv_scale) {
-  if (ST == ST_FP32) return __ldg(static_cast<const float*>(base) + a * plane + idx);
-  if (a == 0) return __ldg(static_cast<const float*>(base) + idx);
+__device__ __forceinline__ unsigned int ld_raw(const void* __restrict__ base, int plane, int a, int idx) {
+  if (ST == ST_FP32) return __float_as_uint(__ldg(static_cast<const float*>(base) + a * plane + idx));
+  if (a == 0) return __float_as_uint(__ldg(static_cast<const float*>(base) + idx));
   const unsigned short* h = reinterpret_cast<const unsigned short*>(static_cast<const float*>(base) + plane);
-  const unsigned short raw = __ldg(h + (a - 1) * plane + idx);
-  const float v = ST == ST_FP16 ? __half2float(__ushort_as_half(raw)) : __bfloat162float(__ushort_as_bfloat16(raw));
+  return __ldg(h + (a - 1) * plane + idx);
+}
+
+template <int ST>
+__device__ __forceinline__ float dec_pop(unsigned int raw, int a, float inv_scale) {
+  if (ST == ST_FP32 || a == 0) return __uint_as_float(raw);
+  const unsigned short r16 = static_cast<unsigned short>(raw);
+  const float v = ST == ST_FP16 ? __half2float(__ushort_as_half(r16)) : __bfloat162float(__ushort_as_bfloat16(r16));
   return __fmul_rn(v, inv_scale);   // never contracted: identical rounding in every kernel
 }
 
@@ -197,18 +205,19 @@ __device__ __forceinline__ void st_pop(void* __restrict__ base, int plane, int a
   }
 }
 
-// Pull the 9 pre-collision populations of one distribution (planes starting at `src`):
+// Pull the 9 pre-collision populations of one distribution (planes starting at `src`), as stored
+// bits (decode with dec_pop at plane FIRST + a):
 // v[a] = P*_a(x - e_a), or P*_opp(a)(x) when x - e_a lies beyond a wall (half-way bounce-back).
 // Cells with no wall neighbour take the branch-free path.
 template <int ST, int FIRST>
 __device__ __forceinline__ void gather9(const void* __restrict__ src, int plane, const ColNb& c, const RowNb& r,
-                                        float inv_scale, float v[Q]) {
+                                        unsigned int v[Q]) {
   if (!(c.wl | c.wr | r.wb | r.wt)) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const int sx = cx(a) == 1 ? c.xm : (cx(a) == -1 ? c.xq : c.x0);
       const int sr = cy(a) == 1 ? r.rm : (cy(a) == -1 ? r.rq : r.r0);
-      v[a] = ld_pop<ST>(src, plane, FIRST + a, sr + sx, inv_scale);
+      v[a] = ld_raw<ST>(src, plane, FIRST + a, sr + sx);
     }
   } else {
 #pragma unroll
@@ -217,8 +226,7 @@ __device__ __forceinline__ void gather9(const void* __restrict__ src, int plane,
       const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && r.wb) || (ey == -1 && r.wt);
       const int sx = ex == 1 ? c.xm : (ex == -1 ? c.xq : c.x0);
       const int sr = ey == 1 ? r.rm : (ey == -1 ? r.rq : r.r0);
-      v[a] = hit ? ld_pop<ST>(src, plane, FIRST + opp(a), r.r0 + c.x0, inv_scale)
-                 : ld_pop<ST>(src, plane, FIRST + a, sr + sx, inv_scale);
+      v[a] = hit ? ld_raw<ST>(src, plane, FIRST + opp(a), r.r0 + c.x0) : ld_raw<ST>(src, plane, FIRST + a, sr + sx);
     }
   }
 }
@@ -471,8 +479,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
     }
   };
 
-  // prefetched gathers: f (+ f_0lo) of the next S0 row, gbar of the next S2 row
-  float fp[NF], gp[Q];
+  // prefetched gathers (stored bits): f (+ f_0lo) of the next S0 row, gbar of the next S2 row
+  unsigned int fpr[NF], gpr[Q];
   auto row_nb = [&](int r, auto checked) {
     if constexpr (decltype(checked)::value) {
       return make_row(wrap1(r, g.ny), g);
@@ -487,12 +495,12 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   };
   auto fetch_f = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
-    gather9<ST, 0>(g.src, g.plane, cn, rn, g.isf, fp);
-    fp[Q] = ST == ST_FP32 ? ld_pop<ST>(g.src, g.plane, PLANE_F0LO, rn.r0 + cn.x0, 1.0f) : 0.0f;
+    gather9<ST, 0>(g.src, g.plane, cn, rn, fpr);
+    fpr[Q] = ST == ST_FP32 ? ld_raw<ST>(g.src, g.plane, PLANE_F0LO, rn.r0 + cn.x0) : 0u;
   };
   auto fetch_g = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
-    gather9<ST, Q>(g.src, g.plane, cn, rn, g.isg, gp);
+    gather9<ST, Q>(g.src, g.plane, cn, rn, gpr);
   };
   auto s0_active = [&](int r) { return r <= yb + 2 && in_w3 && row_ok(r); };
   auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
@@ -510,6 +518,10 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
     const int o4 = slot(a - 4), o5 = slot(a - 5), o6 = slot(a - 6);
     // ---- S0: phi at row a (as an unevaluated pair hi + lo)
     if (IN ? in_w3 : s0_active(a)) {
+      float fp[NF];
+#pragma unroll
+      for (int k = 0; k < Q; ++k) fp[k] = dec_pop<ST>(fpr[k], k, g.isf);
+      fp[Q] = __uint_as_float(fpr[Q]);
       const float small =
           fadd(fp[Q], fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8]))));
       float hi, lo;
@@ -587,7 +599,9 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
             sdef = fmul(P.s_coef6, lmu6);
           }
         }
-        const float* gb = gp;
+        float gb[Q];
+#pragma unroll
+        for (int k = 0; k < Q; ++k) gb[k] = dec_pop<ST>(gpr[k], Q + k, g.isg);
         const float s13 = fadd(gb[1], gb[3]), d13 = fsub(gb[1], gb[3]);
         const float s24 = fadd(gb[2], gb[4]), d24 = fsub(gb[2], gb[4]);
         const float s57 = fadd(gb[5], gb[7]), d57 = fsub(gb[5], gb[7]);
