@@ -78,11 +78,12 @@ def _time(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def tune_sim(sim, storage=0, reps=6, candidates=None, use_cache=True):
+def tune_sim(sim, reps=6, candidates=None, use_cache=True):
     """Measure tile candidates on `sim` (its state advances; re-initialise it afterwards) and
-    set the fastest.  Returns (threads, rows, ms per step)."""
+    set the fastest.  Returns (threads, rows, ms per step).  The cache key includes the
+    simulation's population storage."""
     import torch
-    key = _key("sim", sim.nx, sim.ny, storage)
+    key = _key("sim", sim.nx, sim.ny, int(sim.params.storage))
     with _lock:
         cache = _load() if use_cache else {}
     if key in cache:
@@ -106,15 +107,20 @@ def tune_sim(sim, storage=0, reps=6, candidates=None, use_cache=True):
     return best
 
 
+BATCH_THREADS = (64, 128, 256)
+BATCH_ROWS = (16, 32, 64, 128)
+
+
 def tune_batch(batch, reps=3, candidates=None):
-    """Measure (threads, rows) of the batch kernel on the current membership (members advance)."""
+    """Measure (threads, rows) of the batch kernel on the current membership (members advance).
+    Returns (threads, rows, ms per step)."""
     import torch
     stream = torch.cuda.current_stream()
     best = None
-    for t, r in candidates or [(t, r) for t in (64, 128) for r in (8, 16, 32, 64)]:
+    for t, r in candidates or [(t, r) for t in BATCH_THREADS for r in BATCH_ROWS]:
         batch.set_tile(t, r)
-        ms = _time(lambda: batch.step(2), reps, stream)
+        ms = _time(lambda: batch.step(2), reps, stream) / 2      # per step, like best[2]
         if best is None or ms < best[2]:
-            best = (t, r, ms / 2)
+            best = (t, r, ms)
     batch.set_tile(best[0], best[1])
     return best
