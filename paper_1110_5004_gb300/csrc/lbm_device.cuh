@@ -481,6 +481,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
 
   // prefetched gathers (stored bits): f (+ f_0lo) of the next S0 row, gbar of the next S2 row
   unsigned int fpr[NF], gpr[Q];
+  unsigned int spr[2];                       // direct mass defect: rho, div(rho u) of the last step
   auto row_nb = [&](int r, auto checked) {
     if constexpr (decltype(checked)::value) {
       return make_row(wrap1(r, g.ny), g);
@@ -501,6 +502,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto fetch_g = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
     gather9<ST, Q>(g.src, g.plane, cn, rn, gpr);
+    if constexpr (SD) {
+      const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
+      spr[0] = __float_as_uint(__ldg(sp + rn.r0 + cn.x0));
+      spr[1] = __float_as_uint(__ldg(sp + g.plane + rn.r0 + cn.x0));
+    }
   };
   auto s0_active = [&](int r) { return r <= yb + 2 && in_w3 && row_ok(r); };
   auto s2_active = [&](int r) { return r >= ya - 1 && r <= yb && in_w1 && row_ok(r); };
@@ -589,10 +595,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
         auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
         if (P.remove_Fa || (MODE == MODE_MOMENTS && mo.fax)) {
-          if (SD) {
-            const int ci = cell_of();
-            const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
-            sdef = fadd(fsub(rho, __ldg(sp + ci)), __ldg(sp + g.plane + ci));
+          if constexpr (SD) {
+            sdef = fadd(fsub(rho, __uint_as_float(spr[0])), __uint_as_float(spr[1]));   // prefetched
           } else {
             const float lmu6 = fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
                                                        fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
