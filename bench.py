@@ -106,6 +106,7 @@ class ClockSampler:
         self.proc = None
         self.lines = []
         self.t = None
+        self.first = 0          # index of the first sample taken inside the timed region
 
     def __enter__(self):
         try:
@@ -114,6 +115,12 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # nvidia-smi takes a moment to start: let it deliver a sample before the timed
+            # region begins (bounded wait), and count only the samples taken after that
+            deadline = time.perf_counter() + 3.0
+            while not self.lines and time.perf_counter() < deadline and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.lines)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
@@ -134,7 +141,8 @@ class ClockSampler:
 
     def summary(self):
         rows = []
-        for ln in self.lines:
+        lines = self.lines[self.first:] or self.lines[-1:]
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
