@@ -17,7 +17,7 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_autotune_cache.json")
 THREADS = (64, 128, 256)
-ROWS = (0, 8, 12, 16, 24, 32, 48, 64, 128)
+ROWS = (0, 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 128)
 _lock = threading.Lock()
 
 
