@@ -113,9 +113,9 @@ struct Grid {
   long long spoff;      // s_form 1: byte offset of the [rho, div(rho u)] planes in src/dst (else 0)
 };
 
-// Output planes of the moments mode (row-major with `pitch`).
-// Outputs of the moment pass; each may be null.  fax, fay: the additional interfacial force
-// F_a = -u s of Eq. 12 (s by the simulation's s_form), evaluated whichever scheme runs.
+// Output planes of the moment pass (row-major with `pitch`); each may be null.  fax, fay: the
+// additional interfacial force F_a = -u s of Eq. 12 (s by the simulation's s_form), evaluated
+// whichever scheme runs.
 struct MomentOut {
   float *phi, *rho, *ux, *uy, *p;
   float *fax, *fay;
