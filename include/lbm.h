@@ -90,12 +90,17 @@ extern "C" {
  *                    div(rho u) in two more planes per state buffer (8 B per cell each,
  *                    lbm_sim_device_bytes counts them; at t = 0 the initial fields stand for
  *                    t = -1).
- *   pad           set to 0. */
+ *   f_form        order-parameter LBE (the paper uses a Cahn-Hilliard LBE it does not print):
+ *                 0 (default): BGK towards an equilibrium whose second moment carries the
+ *                 chemical potential; 1: forced form, relaxing to phi omega_a(u) with the
+ *                 forcing (e_a - u).grad(phi) omega_a(u) and the mobility source
+ *                 theta_M lap(mu) omega_a(u).  This library implements 0 only: 1 is rejected
+ *                 with LBM_ERR_INVALID_ARG (the FP64 reference implements both). */
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;
     int ch_conservative, fs_form;
-    int s_form, pad;
+    int s_form, f_form;
 } lbm_params;
 
 /* FP64 diagnostics of the current state (reductions in a fixed order: bitwise reproducible).

@@ -31,7 +31,7 @@ MU, S, FSX, FSY, DPX, DPY, GRAD_PHI_X, GRAD_PHI_Y, LAP_MU, TAU_G, DIVU, FAX, FAY
 class Params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "beta", "kappa", "phi_star", "theta_M", "tau_f", "tau_g_A", "tau_g_B", "rho_A", "rho_B",
-        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form", "s_form", "pad")]
+        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form", "s_form", "f_form")]
 
 
 class Diag(ctypes.Structure):
@@ -124,7 +124,8 @@ def params_from_physical(phys) -> Params:
                   tau_f=phys.tau_f, tau_g_A=tau_from_nu(phys.nu_A), tau_g_B=tau_from_nu(phys.nu_B),
                   rho_A=phys.rho_A, rho_B=phys.rho_B, gravity=phys.gravity, bc_x=phys.bc_x,
                   bc_y=phys.bc_y, remove_Fa=phys.remove_Fa, storage=0,
-                  ch_conservative=phys.ch_conservative, fs_form=phys.fs_form, s_form=phys.s_form)
+                  ch_conservative=phys.ch_conservative, fs_form=phys.fs_form, s_form=phys.s_form,
+                  f_form=phys.f_form)
 
 
 def set_threads(n: int):

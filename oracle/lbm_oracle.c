@@ -32,6 +32,13 @@
  *   f^eq_a (a != 0) = w_a [Gamma_f mu / cs2 + phi (e.u/cs2 + (e.u)^2/(2 cs2^2) - u^2/(2 cs2))],
  *   f^eq_0 = phi - sum_{a != 0} f^eq_a,  Gamma_f = theta_M / (tau_f - 1/2)   (recovers Eq. 2)
  *   f_a(x + e_a, t+1) = f_a - (f_a - f^eq_a)/tau_f + w_a phi div(u)   [convective form]
+ *   f_form = 1 (forced order-parameter LBE) instead relaxes f to phi Gamma_a and adds
+ *     (1 - 1/(2 tau_f)) (e_a - u).grad(phi) Gamma_a + theta_M lap(mu) Gamma_a:
+ *     f_a(x + e_a, t+1) = f_a - (f_a - phi Gamma_a)/tau_f + (1 - 1/(2 tau_f)) (e_a - u).grad(phi) Gamma_a
+ *                         + theta_M lap(mu) Gamma_a + w_a phi div(u)   [convective form]
+ *     The first moment of the grad(phi) term, cs2 grad(phi), cancels the lattice diffusion
+ *     cs2 (tau_f - 1/2) lap(phi) of the phi Gamma_a equilibrium; the mobility enters as the
+ *     zeroth-moment source div(theta_M grad mu), applied in full each step.
  *   The moments of f^eq make the f-LBE recover d_t phi + div(phi u) = div(theta_M grad mu);
  *   Eq. 2 is the convective form d_t phi + u.grad(phi) = div(theta_M grad mu).  The two differ
  *   by phi div(u), which the weakly compressible flow does not make zero; the source
@@ -69,7 +76,7 @@ typedef struct {
     int ch_conservative;    /* 0: convective Cahn-Hilliard (Eq. 2), 1: conservative form */
     int fs_form;            /* 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi) */
     int s_form;             /* 0: s by Eq. 5, 1: s from the stored rho and div(rho u) */
-    int pad;
+    int f_form;             /* 0: f^eq carrying the mu term, 1: forced order-parameter LBE */
 } orc_params;
 
 typedef struct {
@@ -313,7 +320,8 @@ int lbm_init_fields_ref(orc_sim* s, const double* phi0, const double* ux0, const
         orc_node_equilibria(P, s->phi[i], s->mu[i], density(P, s->phi[i]), p, ux, uy, feq, geq,
                             NULL);
         for (int a = 0; a < Q; ++a) {
-            s->f[a * N + i] = feq[a];
+            /* f_form 1 relaxes f to phi Gamma_a: start there */
+            s->f[a * N + i] = P->f_form ? s->phi[i] * omega_a(a, ux, uy) : feq[a];
             s->g[a * N + i] = geq[a];
         }
         s->rho[i] = density(P, s->phi[i]);
@@ -427,7 +435,17 @@ static void collide(orc_sim* s) {
             double gv = s->g[a * N + i];
             s->gs[a * N + i] = gv - (gv - geq[a]) / tg + (1.0 - 1.0 / (2.0 * tg)) * S[a];
             double fv = s->f[a * N + i];
-            s->fs[a * N + i] = fv - (fv - feq[a]) / tf + (P->ch_conservative ? 0.0 : WT[a] * ph * s->divu[i]);
+            double src = P->ch_conservative ? 0.0 : WT[a] * ph * s->divu[i];
+            if (P->f_form) {
+                /* forced order-parameter LBE: equilibrium phi Gamma_a, forcing (e_a - u).grad(phi)
+                   Gamma_a (trapezoidal weight) and the mobility source theta_M lap(mu) Gamma_a */
+                double Ga = omega_a(a, ux, uy);
+                double ef = (EX[a] - ux) * s->gpx[i] + (EY[a] - uy) * s->gpy[i];
+                s->fs[a * N + i] = fv - (fv - ph * Ga) / tf + (1.0 - 1.0 / (2.0 * tf)) * ef * Ga +
+                                   P->theta_M * s->lmu[i] * Ga + src;
+            } else {
+                s->fs[a * N + i] = fv - (fv - feq[a]) / tf + src;
+            }
         }
     }
 }

@@ -66,7 +66,8 @@ def params_from_physical(phys, storage=LBM_FP32) -> lbm_params:
                       tau_g_B=lib().lbm_tau_from_nu(phys.nu_B), rho_A=phys.rho_A,
                       rho_B=phys.rho_B, gravity=phys.gravity, bc_x=phys.bc_x, bc_y=phys.bc_y,
                       remove_Fa=phys.remove_Fa, storage=storage,
-                      ch_conservative=phys.ch_conservative, fs_form=phys.fs_form, s_form=phys.s_form)
+                      ch_conservative=phys.ch_conservative, fs_form=phys.fs_form, s_form=phys.s_form,
+                      f_form=phys.f_form)
 
 
 def device_bytes(nx, ny, storage=LBM_FP32) -> int:

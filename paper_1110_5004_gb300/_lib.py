@@ -31,7 +31,7 @@ EXPORTS = (
 class lbm_params(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "beta", "kappa", "phi_star", "theta_M", "tau_f", "tau_g_A", "tau_g_B", "rho_A", "rho_B",
-        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form", "s_form", "pad")]
+        "gravity")] + [(n, ctypes.c_int) for n in ("bc_x", "bc_y", "remove_Fa", "storage", "ch_conservative", "fs_form", "s_form", "f_form")]
 
 
 class lbm_diag(ctypes.Structure):

@@ -124,6 +124,7 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("ch_conservative must be 0 or 1"), LBM_ERR_INVALID_ARG;
   if (p->fs_form != 0 && p->fs_form != 1) return set_error("fs_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
   if (p->s_form != 0 && p->s_form != 1) return set_error("s_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
+  if (p->f_form != 0) return set_error("f_form 1 (forced order-parameter LBE) is not implemented here"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 

@@ -495,6 +495,69 @@ def test_diagnostics_against_geometry():
     assert not oracle.Sim.from_workload(w).diagnostics()["finite"]
 
 
+def iso_lap_periodic(a):
+    """The isotropic 9-point Laplacian with periodic wrap, written out here."""
+    P = np.pad(a, 1, mode="wrap")
+    c = slice(1, -1)
+    ax = P[c, 2:] + P[c, :-2] + P[2:, c] + P[:-2, c]
+    dg = P[2:, 2:] + P[2:, :-2] + P[:-2, 2:] + P[:-2, :-2]
+    return (4 * ax + dg - 20 * a) / 6
+
+
+def iso_grad_periodic(a):
+    P = np.pad(a, 1, mode="wrap")
+    c = slice(1, -1)
+    gx = (4 * (P[c, 2:] - P[c, :-2]) + (P[2:, 2:] - P[2:, :-2]) + (P[:-2, 2:] - P[:-2, :-2])) / 12
+    gy = (4 * (P[2:, c] - P[:-2, c]) + (P[2:, 2:] - P[:-2, 2:]) + (P[2:, :-2] - P[:-2, :-2])) / 12
+    return gx, gy
+
+
+@pytest.mark.parametrize("ch", [0, 1])
+def test_forced_order_parameter_collision(ch):
+    """f_form = 1: the f collision relaxes to phi Gamma_a(u) and adds the forcing
+    (1 - 1/(2 tau_f)) (e_a - u).grad(phi) Gamma_a and the mobility source theta_M lap(mu) Gamma_a.
+    Its zeroth moment changes phi by exactly theta_M lap(mu) (+ phi div(u) in the convective
+    form); its first moment moves by the BGK relaxation towards phi u plus
+    (1 - 1/(2 tau_f)) cs2 grad(phi) + theta_M lap(mu) u; with the test's own stencils."""
+    w = W.random_small(30, 22, seed=19, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, f_form=1, ch_conservative=ch))
+    s = oracle.Sim.from_workload(w)
+    s.step(7)
+    f, _ = s.get_state()
+    m = s.moments()
+    fst, _ = s.collide()
+    phi, ux, uy = m["phi"], m["ux"], m["uy"]
+    lmu = iso_lap_periodic(s.field(oracle.MU))
+    thM, tf = w.phys.theta_M, w.phys.tau_f
+    div = 0.0 if ch else phi * iso_div(ux, uy, W.PERIODIC, W.PERIODIC)
+    np.testing.assert_allclose(fst.sum(0) - f.sum(0), thM * lmu + div, atol=1e-14)
+    gx, gy = iso_grad_periodic(phi)
+    jx, jy = np.tensordot(EX, f, axes=1), np.tensordot(EY, f, axes=1)
+    ex = (1 - 1 / tf) * jx + phi * ux / tf + (1 - 0.5 / tf) * CS2 * gx + thM * lmu * ux
+    ey = (1 - 1 / tf) * jy + phi * uy / tf + (1 - 0.5 / tf) * CS2 * gy + thM * lmu * uy
+    np.testing.assert_allclose(np.tensordot(EX, fst, axes=1), ex, atol=1e-14)
+    np.testing.assert_allclose(np.tensordot(EY, fst, axes=1), ey, atol=1e-14)
+
+
+def test_forced_order_parameter_keeps_a_translating_drop_bounded():
+    """A drop (rho 10 : 1, W = 3, sigma = 1e-4) set moving at U = 0.01 through a periodic box:
+    with the forced order-parameter LBE phi stays within 10 % of phi* for 600 steps, where the
+    equilibrium form with the mu term overshoots ever further and leaves the finite range."""
+    n, U = 96, 0.01
+    base = W.static_droplet(nx=n, ny=n, R=16.0, W=3.0, sigma=1e-4, ratio=10.0, tau=0.65)
+    base = dataclasses.replace(base, uy0=np.full((n, n), -U, np.float32),
+                               phys=dataclasses.replace(base.phys, tau_f=0.8))
+    out = {}
+    for ff in (0, 1):
+        w = dataclasses.replace(base, phys=dataclasses.replace(base.phys, f_form=ff))
+        s = oracle.Sim.from_workload(w)
+        s.step(600)
+        phi = s.moments()["phi"]
+        out[ff] = float(np.nanmin(phi)) if np.isfinite(phi).all() else -np.inf
+    assert out[1] > -1.1
+    assert out[0] < out[1] - 0.1
+
+
 def test_surface_force_forms():
     """F_s = mu grad(phi) (fs_form = 1) and -phi grad(mu) (fs_form = 0), each against the
     product of the oracle's phi and mu with the test's own isotropic gradient."""
@@ -520,8 +583,9 @@ def test_surface_force_forms():
         np.testing.assert_allclose(s.field(oracle.FSY), ey, atol=1e-15)
 
 
+@pytest.mark.parametrize("ff", [0, 1])
 @pytest.mark.parametrize("ch", [1, 0])
-def test_linear_cahn_hilliard_decay(ch):
+def test_linear_cahn_hilliard_decay(ch, ff):
     """Eq. 2 linearised about a uniform phi0 (theta''(phi0) > 0).  A mode cos(kx) has
     mu' = M phi' with M = theta''(phi0) + kappa lam, lam = 2 (1 - cos k) the discrete Laplacian
     symbol.
@@ -530,11 +594,15 @@ def test_linear_cahn_hilliard_decay(ch):
     Conservative form (ch_conservative = 1): force balance grad(p) = -phi0 grad(mu') with
     d_t p = -rho cs2 div(u) (Eq. 9) gives a flow whose flux phi0 u slows the decay:
         rate = theta_M lam M / (1 + phi0^2 M / (rho cs2)).
-    theta_M = Gamma_f (tau_f - 1/2) is the mobility of the Cahn-Hilliard equilibrium.  Checked
-    within 2 % after the acoustic transient; the two forms differ by ~27 % here."""
-    nx, ny, phi0, eps = 32, 4, 0.8, 1e-4
+    theta_M = Gamma_f (tau_f - 1/2) is the mobility of the Cahn-Hilliard equilibrium, or that of
+    the source of the forced order-parameter LBE (f_form = 1, same closed forms).  Checked
+    within 2 % after the acoustic transient; the two forms differ by ~27 % here.  The forced
+    form's grad(phi) forcing (isotropic central differences) cancels the streaming's lattice
+    diffusion cs2 (tau_f - 1/2) lap(phi) only to second order: a residual of order k^4 remains
+    (6 % at 32 cells per wavelength), so that form is checked at 64, where it is below 2 %."""
+    nx, ny, phi0, eps = (32 if ff == 0 else 64), 4, 0.8, 1e-4
     sigma, Wd, thM, rho = 0.1, 2.0, 0.1, 1.0
-    phys = W.Physical(sigma=sigma, W=Wd, theta_M=thM, rho_A=rho, rho_B=rho, ch_conservative=1 - ch)
+    phys = W.Physical(sigma=sigma, W=Wd, theta_M=thM, rho_A=rho, rho_B=rho, ch_conservative=1 - ch, f_form=ff)
     k = 2 * np.pi / nx
     xs = np.arange(nx)
     phi = phi0 + eps * np.cos(k * xs)[None, :].repeat(ny, 0)
@@ -545,12 +613,13 @@ def test_linear_cahn_hilliard_decay(ch):
     plain = thM * lam * M
     rate = plain if ch else plain / (1 + phi0 ** 2 * M / (rho * CS2))
     amps, ts = [], []
-    s.step(1500)
+    t0, dt = (1500, 300) if ff == 0 else (3000, 1200)
+    s.step(t0)
     for t in range(6):
         m = s.moments()["phi"][0]
         amps.append(2 * np.mean((m - m.mean()) * np.cos(k * xs)))
-        ts.append(1500 + 300 * t)
-        s.step(300)
+        ts.append(t0 + dt * t)
+        s.step(dt)
     fit = -np.polyfit(ts, np.log(amps), 1)[0]
     assert fit == pytest.approx(rate, rel=0.02)
     if not ch:

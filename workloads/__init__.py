@@ -63,6 +63,7 @@ class Physical:
     ch_conservative: int = 0  # 0: convective Cahn-Hilliard equation (as printed), 1: conservative form
     fs_form: int = 0        # 0: F_s = -phi grad(mu), 1: F_s = mu grad(phi)
     s_form: int = 0         # mass defect s: 0 by Eq. 5, 1 from the stored rho and div(rho u)
+    f_form: int = 0         # order-parameter LBE: 0 mu-term equilibrium, 1 forced (equilibrium phi Gamma)
 
 
 @dataclasses.dataclass
