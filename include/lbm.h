@@ -94,8 +94,8 @@ extern "C" {
  *                 0 (default): BGK towards an equilibrium whose second moment carries the
  *                 chemical potential; 1: forced form, relaxing to phi omega_a(u) with the
  *                 forcing (e_a - u).grad(phi) omega_a(u) and the mobility source
- *                 theta_M lap(mu) omega_a(u).  This library implements 0 only: 1 is rejected
- *                 with LBM_ERR_INVALID_ARG (the FP64 reference implements both). */
+ *                 theta_M lap(mu) omega_a(u).  1 needs FP32 storage (its populations are O(phi))
+ *                 and cannot join a batch; both are rejected with LBM_ERR_INVALID_ARG. */
 typedef struct {
     double beta, kappa, phi_star, theta_M, tau_f, tau_g_A, tau_g_B, rho_A, rho_B, gravity;
     int bc_x, bc_y, remove_Fa, storage;

@@ -56,6 +56,9 @@ Phys make_phys(const lbm_params& p) {
   P.mu3_d = (float)(3.0 * (p.rho_A * cs2 * (p.tau_g_A - 0.5) - p.rho_B * cs2 * (p.tau_g_B - 0.5)));
   P.keep_f = (float)(1.0 - 1.0 / p.tau_f);
   P.of3gf = (float)(3.0 * p.theta_M / (p.tau_f - 0.5) / p.tau_f);
+  P.f_forced = p.f_form ? 1 : 0;
+  P.hf12 = (float)((1.0 - 0.5 / p.tau_f) / 12.0);
+  P.thM6 = (float)(p.theta_M / 6.0);
   return P;
 }
 
@@ -124,7 +127,9 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("ch_conservative must be 0 or 1"), LBM_ERR_INVALID_ARG;
   if (p->fs_form != 0 && p->fs_form != 1) return set_error("fs_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
   if (p->s_form != 0 && p->s_form != 1) return set_error("s_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
-  if (p->f_form != 0) return set_error("f_form 1 (forced order-parameter LBE) is not implemented here"), LBM_ERR_INVALID_ARG;
+  if (p->f_form != 0 && p->f_form != 1) return set_error("f_form must be 0 or 1"), LBM_ERR_INVALID_ARG;
+  if (p->f_form && p->storage != LBM_FP32)
+    return set_error("f_form 1 needs FP32 storage (its populations are O(phi))"), LBM_ERR_INVALID_ARG;
   return LBM_OK;
 }
 

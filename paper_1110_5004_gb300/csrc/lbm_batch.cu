@@ -209,6 +209,9 @@ int lbm_batch_add(lbm_batch* b, lbm_sim* s, int* slot) {
   Range range_("lbm_batch_add");
   if (!b || !s) return set_error("batch and sim are required"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation already belongs to a batch"), LBM_ERR_INVALID_ARG;
+  if (s->params.f_form)
+    return set_error("f_form 1 simulations are stepped alone (the batch kernel has no forced form)"),
+           LBM_ERR_INVALID_ARG;
   const size_t need = lbm_sim_device_bytes(s);
   if (b->budget && b->bytes + need > b->budget) {
     set_error("batch budget: %zu + %zu > %zu bytes", b->bytes, need, b->budget);

@@ -84,6 +84,9 @@ struct Phys {
   int ch_conv;          // 1: the f collision adds w_a phi div(u) (convective Cahn-Hilliard form)
   int fs_mu;            // 1: F_s = mu grad(phi); 0: F_s = -phi grad(mu)
   int s_direct;         // 1: s = (rho - rho_prev) + div(rho u)_prev from the state's extra planes
+  int f_forced;         // 1: forced order-parameter LBE (equilibrium phi Gamma_a)
+  float hf12;           // (1 - omega_f / 2) / 12: weight of its grad(phi) forcing (12 grad phi)
+  float thM6;           // theta_M / 6: its mobility source from 6 lap(mu)
 };
 
 // Geometry and buffers of one simulation as the kernels see them.
@@ -260,6 +263,8 @@ struct Rec {
   float mrx3, mry3;     // -(grad rho) / 3
   float og;             // omega_g = 1 / tau_g(phi)
   float ogr3;           // omega_g rho / 3
+  float gx12, gy12;     // forced order-parameter form: 12 grad(phi)
+  float lmu6;           // and 6 lap(mu)
 };
 
 constexpr int RING = 8;      // rows of phi (hi, lo), mu and p, incl. one mirrored ghost row at a wall
@@ -288,6 +293,9 @@ enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
 //   S_a    = (e_a - u).[F Gamma_a - gmw_a grad psi] = w_a (e_a.F - u.F) + gmw_a (e_a.D - u.D)
 //   gbar*_a = (1 - omega_g) gbar_a + omega_g g^eq_a + (1 - omega_g / 2) S_a
 //   f*_a   = (1 - omega_f) f_a + omega_f w_a (3 Gamma_f mu + phi poly_a) + w_a phi div(u)   (a > 0)
+// or, in the forced order-parameter form (FF), with h = 1 - omega_f / 2:
+//   f*_a   = (1 - omega_f) f_a + Gamma_a [omega_f phi + h (e_a - u).grad phi + theta_M lap mu]
+//            + w_a phi div(u)
 // The weight-class products are formed once per cell (class 0: rest, 1: axis, 2: diagonal).
 struct CollideC {
   float ux, uy, up, um, m15uu;
@@ -298,9 +306,11 @@ struct CollideC {
   float ogr3, keep_g, src_g, keep_f;
   float ofwg[3];    // omega_f w_c 3 Gamma_f mu
   float ofwp[3];    // omega_f w_c phi
+  float hgx, hgy, hgp, hgm, c0, ofp;   // FF: h grad(phi) projections; theta_M lap mu - h u.grad phi; omega_f phi
+  float wphiD[3];   // FF: w_c phi div(u)
 };
 
-template <int ST, int A>
+template <int ST, int A, bool FF>
 __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q], const float gb[Q], const Grid& g,
                                             int cell, float& fsum, float& ofeqsum) {
   constexpr int C = A == 0 ? 0 : (A <= 4 ? 1 : 2);
@@ -320,7 +330,14 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
   const float S = fmad(gmw, t2, t1w);
   st_pop<ST>(g.dst, g.plane, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
   if (A > 0) {
-    const float ofeq = fmad(k.ofwp[C], poly, k.ofwg[C]);
+    float ofeq;
+    if constexpr (FF) {
+      const float Ga = fadd(w, gmw);                                        // Gamma_a
+      const float ta = fadd(eproj<A>(k.hgx, k.hgy, k.hgp, k.hgm), k.c0);    // h (e_a - u).grad phi + theta_M lap mu
+      ofeq = fmad(Ga, fadd(ta, k.ofp), k.wphiD[C]);
+    } else {
+      ofeq = fmad(k.ofwp[C], poly, k.ofwg[C]);
+    }
     fsum = fadd(fsum, f[A]);
     ofeqsum = fadd(ofeqsum, ofeq);
     st_pop<ST>(g.dst, g.plane, A, cell, fmad(k.keep_f, f[A], ofeq), g.sf);
@@ -330,7 +347,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
 // Collision of both distributions at one cell and store of the post-collision populations.
 // f[] holds f_1..f_8 (index 0 unused), gb[] gbar_0..gbar_8; gpx12/gpy12 are 12 grad p.
 // phiD = phi div(u) (convective form) or 0: the f collision adds w_a phiD to direction a.
-template <int ST>
+template <int ST, bool FF>
 __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx12, float gpy12,
                                               float phi_hi, float phi_lo, float phiD, const float f[Q],
                                               const float gb[Q], const Grid& g, int cell) {
@@ -368,23 +385,41 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   k.ofwg[2] = fmul(1.0f / 36.0f, ofg);
   k.ofwp[1] = fmul(1.0f / 9.0f, ofp);
   k.ofwp[2] = fmul(1.0f / 36.0f, ofp);
+  if constexpr (FF) {
+    const float hx = fmul(P.hf12, r.gx12), hy = fmul(P.hf12, r.gy12);
+    k.hgx = hx;
+    k.hgy = hy;
+    k.hgp = fadd(hx, hy);
+    k.hgm = fsub(hx, hy);
+    k.c0 = fsub(fmul(P.thM6, r.lmu6), fmad(r.ux, hx, fmul(r.uy, hy)));
+    k.ofp = ofp;
+    k.wphiD[0] = 0.0f;
+    k.wphiD[1] = fmul(1.0f / 9.0f, phiD);
+    k.wphiD[2] = fmul(1.0f / 36.0f, phiD);
+  }
   float fsum = 0.0f, ofeqsum = 0.0f;
-  collide_dir<ST, 0>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 1>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 2>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 3>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 4>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 5>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 6>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 7>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 8>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 0, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 1, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 2, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 3, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 4, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 5, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 6, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 7, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 8, FF>(k, f, gb, g, cell, fsum, ofeqsum);
   // f_0 = phi - sum_{a>0} f_a and omega_f (f_0^eq - f_0) = omega_f sum_{a>0} f_a - sum omega_f f^eq_a;
   // the directions a > 0 carry w_a phiD of the source inside ofeqsum, so the rest gets
   // phiD - (5/9) phiD = w_0 phiD by adding phiD:
   // f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum (omega_f f^eq_a + w_a phiD)) + phiD].
   // Only small terms are rounded before the one error-free sum with the O(1) high word.
   float hi, lo;
-  two_sum(phi_hi, fadd(fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), phiD), hi, lo);
+  if constexpr (FF) {
+    // the forced form changes phi by theta_M lap mu (+ phiD) in the collision
+    two_sum(phi_hi, fadd(fadd(fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), fmul(P.thM6, r.lmu6)), phiD),
+            hi, lo);
+  } else {
+    two_sum(phi_hi, fadd(fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), phiD), hi, lo);
+  }
   if (ST == ST_FP32) {
     st_pop<ST>(g.dst, g.plane, 0, cell, hi, 1.0f);
     st_pop<ST>(g.dst, g.plane, PLANE_F0LO, cell, lo, 1.0f);
@@ -403,7 +438,8 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
 // and the stencils have radius 1.
 // Inlined into both kernels; its arithmetic is fixed by the explicit intrinsics above.
 // SD: the direct mass defect (s_form 1) is compiled in; kernels without it carry none of its code.
-template <int NT, int MODE, int ST, bool SD>
+// FF: the forced order-parameter LBE (f_form 1; FP32 storage only).
+template <int NT, int MODE, int ST, bool SD, bool FF = false>
 __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
                                       Smem<NT>& sm) {
   const int t = threadIdx.x;
@@ -594,13 +630,15 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         float sdef = 0.0f;
         // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
         auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
+        auto lap6_mu = [&]() {   // 6 lap(mu)
+          return fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
+                                          fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
+        };
         if (P.remove_Fa || (MODE == MODE_MOMENTS && mo.fax)) {
           if constexpr (SD) {
             sdef = fadd(fsub(rho, __uint_as_float(spr[0])), __uint_as_float(spr[1]));   // prefetched
           } else {
-            const float lmu6 = fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
-                                                       fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
-            sdef = fmul(P.s_coef6, lmu6);
+            sdef = fmul(P.s_coef6, lap6_mu());
           }
         }
         float gb[Q];
@@ -654,6 +692,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
           const float muv3 = fmad(cl, P.mu3_d, P.mu3_B);                  // 3 mu(phi)
           cur.og = __fdividef(1.0f, fmad(muv3, rrho, 0.5f));              // 1 / tau_g(phi)
           cur.ogr3 = fmul(cur.og, fmul(rho, 1.0f / 3.0f));
+          if constexpr (FF) {
+            cur.gx12 = gphx;
+            cur.gy12 = gphy;
+            cur.lmu6 = lap6_mu();
+          }
         }
       }
       if (IN || s2_active(r + 1)) fetch_g(r + 1, CK{});
@@ -712,7 +755,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
           float* sp = reinterpret_cast<float*>(static_cast<char*>(g.dst) + g.spoff);
           sp[g.plane + r * g.pitch + xp] = fmul(fadd(djx, djy), 1.0f / 12.0f);
         }
-        collide_store<ST>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], phiD,
+        collide_store<ST, FF>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], phiD,
                           f, gb, g, r * g.pitch + xp);
       }
     }

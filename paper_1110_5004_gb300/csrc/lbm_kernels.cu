@@ -8,34 +8,41 @@ namespace lbm {
 
 // ------------------------------------------------------------------ fused step / moments
 
-template <int NT, int MODE, int ST, bool SD>
+template <int NT, int MODE, int ST, bool SD, bool FF>
 // 512 / NT resident CTAs per SM (16 warps): caps the registers at 128 per thread.
 __global__ void __launch_bounds__(NT, 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
   const int strip = blockIdx.x % g.n_strips;
   const int seg = blockIdx.x / g.n_strips;
-  run_tile<NT, MODE, ST, SD>(P, g, mo, strip, seg, sm);
+  run_tile<NT, MODE, ST, SD, FF>(P, g, mo, strip, seg, sm);
 }
 
 static int n_tiles(const Grid& g) { return g.n_strips * ((g.ny + g.seg_h - 1) / g.seg_h); }
 
-template <int NT, int MODE, int ST, bool SD>
+template <int NT, int MODE, int ST, bool SD, bool FF>
 static cudaError_t launch_sd(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
   static bool attr_set = false;   // one GPU per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST, SD, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sizeof(Smem<NT>));
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_tiles<NT, MODE, ST, SD><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
+  k_tiles<NT, MODE, ST, SD, FF><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
   return cudaGetLastError();
 }
 
 template <int NT, int MODE, int ST>
 static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
-  return P.s_direct ? launch_sd<NT, MODE, ST, true>(P, g, mo, st) : launch_sd<NT, MODE, ST, false>(P, g, mo, st);
+  // the forced order-parameter form changes only the step's f collision (FP32 storage only)
+  if constexpr (MODE == MODE_STEP && ST == ST_FP32) {
+    if (P.f_forced)
+      return P.s_direct ? launch_sd<NT, MODE, ST, true, true>(P, g, mo, st)
+                        : launch_sd<NT, MODE, ST, false, true>(P, g, mo, st);
+  }
+  return P.s_direct ? launch_sd<NT, MODE, ST, true, false>(P, g, mo, st)
+                    : launch_sd<NT, MODE, ST, false, false>(P, g, mo, st);
 }
 
 template <int MODE, int ST>
@@ -62,9 +69,9 @@ template <int NT>
 static int occupancy_nt() {
   int occ = 0;
   // the dynamic shared-memory size above 48 KB is only admitted once the attribute is set
-  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP, ST_FP32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaFuncSetAttribute(k_tiles<NT, MODE_STEP, ST_FP32, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)sizeof(Smem<NT>));
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP, ST_FP32, false>, NT, sizeof(Smem<NT>));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_tiles<NT, MODE_STEP, ST_FP32, false, false>, NT, sizeof(Smem<NT>));
   cudaGetLastError();
   return occ > 0 ? occ : 1;
 }
@@ -152,7 +159,9 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   #pragma unroll
         for (int k = 1; k < Q; ++k) {
           const float ek = (float)cx(k) * u + (float)cy(k) * v;
-          rest += wgt(k) * (P.three_gamma_f * m + ph * (3.0f * ek + 4.5f * ek * ek - uu15));
+          const float pk = 3.0f * ek + 4.5f * ek * ek - uu15;
+          // f^eq_k: with the mu term, or phi Gamma_k in the forced order-parameter form
+          rest += wgt(k) * (P.f_forced ? ph * (1.0f + pk) : P.three_gamma_f * m + ph * pk);
         }
         float hi, lo;
         two_sum(ph, -rest, hi, lo);
@@ -163,7 +172,8 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
           st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi + lo, 1.0f);
         }
       } else {
-        st_pop<ST>(g.dst, g.plane, a, (int)cell, w * (P.three_gamma_f * m + ph * poly), g.sf);
+        st_pop<ST>(g.dst, g.plane, a, (int)cell,
+                   w * (P.f_forced ? ph * (1.0f + poly) : P.three_gamma_f * m + ph * poly), g.sf);
       }
       st_pop<ST>(g.dst, g.plane, Q + a, (int)cell, geq, g.sg);
     }

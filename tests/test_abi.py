@@ -75,6 +75,8 @@ def _params(**kw):
     (16, 16, {"ch_conservative": 2}, b"ch_conservative"),
     (16, 16, {"fs_form": -1}, b"fs_form"),
     (16, 16, {"s_form": 5}, b"s_form"),
+    (16, 16, {"f_form": 2}, b"f_form"),
+    (16, 16, {"f_form": 1, "storage": 1}, b"FP32"),
 ])
 def test_invalid_arguments_rejected_on_host(L, nx, ny, kw, msg):
     h = ctypes.c_void_p()
@@ -102,7 +104,7 @@ def test_params_layout_zero_defaults():
     the struct is 10 doubles + 8 ints with no padding, as include/lbm.h declares it."""
     from paper_1110_5004_gb300 import lbm_params
     p = lbm_params()
-    assert (p.ch_conservative, p.fs_form, p.s_form, p.remove_Fa) == (0, 0, 0, 0)
+    assert (p.ch_conservative, p.fs_form, p.s_form, p.f_form, p.remove_Fa) == (0, 0, 0, 0, 0)
     assert ctypes.sizeof(lbm_params) == 10 * 8 + 8 * 4
 
 

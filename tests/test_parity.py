@@ -102,6 +102,40 @@ def test_direct_mass_defect(lbm, bcx, bcy):
     assert_parity(got, ref, w)
 
 
+@pytest.mark.parametrize("bcx,bcy,ch,rf,sform", [
+    (W.PERIODIC, W.PERIODIC, 0, 0, 0), (W.PERIODIC, W.WALL, 0, 1, 0), (W.WALL, W.WALL, 1, 1, 0),
+    (W.PERIODIC, W.WALL, 0, 1, 1), (W.WALL, W.PERIODIC, 1, 0, 0)])
+def test_forced_order_parameter_form(lbm, bcx, bcy, ch, rf, sform):
+    """f_form = 1 (forced order-parameter LBE) against the oracle in the same form: periodic and
+    walled boxes, both Cahn-Hilliard forms, F_a kept and removed, both mass-defect forms."""
+    import dataclasses
+    w = W.random_small(71, 39, seed=31 + ch + 2 * rf, bc_x=bcx, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0,
+                       remove_Fa=rf)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, f_form=1, ch_conservative=ch, s_form=sform))
+    _, got, ref = run_both(lbm, w, 200, tile=(64, 9))
+    assert_parity(got, ref, w)
+
+
+def test_forced_form_tiles_and_batch(lbm):
+    """The forced form's results do not depend on the tile shape (bitwise), and a forced
+    simulation cannot join a batch."""
+    import dataclasses
+    w = W.random_small(130, 44, seed=37, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, f_form=1))
+    outs = []
+    for tile in ((64, 5), (128, 16), (256, 44)):
+        s = lbm.Sim.from_workload(w, tile=tile)
+        s.step(25)
+        outs.append(s.moments())
+    for o in outs[1:]:
+        for k in o:
+            assert np.array_equal(o[k], outs[0][k]), k
+    b = lbm.Batch()
+    with pytest.raises(Exception):
+        b.add(lbm.Sim.from_workload(w))
+    b.close()
+
+
 @pytest.mark.parametrize("rf,sform,bcy", [(0, 0, W.WALL), (1, 0, W.PERIODIC), (0, 1, W.WALL), (1, 1, W.PERIODIC)])
 def test_interfacial_force_field(lbm, rf, sform, bcy):
     """F_a = -u s (Eq. 12) of the GPU state against the oracle's, with F_a kept and removed and
