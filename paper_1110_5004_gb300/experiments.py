@@ -12,6 +12,9 @@ both schemes) every `every` steps and, optionally, density and F_a,y fields (the
 at chosen steps; a run that leaves the finite range stops there and reports the step (the
 scheme, not the kernel: the FP64 oracle diverges at the same step).
 
+Both tests run under each order-parameter LBE: the equilibrium form with the mu term, and the
+forced form (f_form = 1), under which the splash stays finite to the paper's t* = 2.
+
   python -m paper_1110_5004_gb300.experiments [--out results.json] [--falling-steps 19000]
 """
 from __future__ import annotations
@@ -80,12 +83,19 @@ def _direct_defect(w):
     return dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
 
 
-def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None, direct_defect=False):
+def _with_f_form(w, f_form):
+    import dataclasses
+    return dataclasses.replace(w, phys=dataclasses.replace(w.phys, f_form=int(f_form)))
+
+
+def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None, direct_defect=False, f_form=0):
     """direct_defect: also run the corrected scheme with the mass defect taken directly from the
-    stored density and flux (s_form = 1) instead of Eq. 5, to see how F_a depends on it."""
+    stored density and flux (s_form = 1) instead of Eq. 5, to see how F_a depends on it.
+    f_form: the order-parameter LBE (0: equilibrium with the mu term, 1: forced form)."""
     import workloads as W
-    res = run_pair(lambda remove_Fa: W.paper_falling_droplet(steps=steps, remove_Fa=remove_Fa), steps, every,
-                   snapshot_steps, stream, {"corrected_direct_s": _direct_defect} if direct_defect else None)
+    res = run_pair(lambda remove_Fa: _with_f_form(W.paper_falling_droplet(steps=steps, remove_Fa=remove_Fa), f_form),
+                   steps, every, snapshot_steps, stream,
+                   {"corrected_direct_s": _direct_defect} if direct_defect else None)
     t, dr = difference(res)
     _, dy = difference(res, "centroid_y")
     r0 = res["original"]["series"]["spread_radius"][0]
@@ -105,10 +115,11 @@ def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None, direct_
     return res
 
 
-def splash(Re, steps=3000, every=50, snapshot_steps=(), stream=None):
+def splash(Re, steps=3000, every=50, snapshot_steps=(), stream=None, f_form=0):
+    """f_form: the order-parameter LBE (0: equilibrium with the mu term, 1: forced form)."""
     import workloads as W
-    res = run_pair(lambda remove_Fa: W.paper_splash(Re=Re, steps=steps, remove_Fa=remove_Fa), steps, every,
-                   snapshot_steps, stream)
+    res = run_pair(lambda remove_Fa: _with_f_form(W.paper_splash(Re=Re, steps=steps, remove_Fa=remove_Fa), f_form),
+                   steps, every, snapshot_steps, stream)
     t, dr = difference(res)
     # Fig. 3 shows F_a,y of the original scheme at t* = 1.8; report it there, or at the last
     # finite diagnostic before it
@@ -143,7 +154,10 @@ def main():
     args = ap.parse_args()
     res = {"falling_drop": falling_drop(args.falling_steps, direct_defect=True),
            "splash_Re48": splash(48.0, args.splash_steps),
-           "splash_Re480": splash(480.0, args.splash_steps)}
+           "splash_Re480": splash(480.0, args.splash_steps),
+           "falling_drop_forced": falling_drop(args.falling_steps, f_form=1),
+           "splash_Re48_forced": splash(48.0, args.splash_steps, f_form=1),
+           "splash_Re480_forced": splash(480.0, args.splash_steps, f_form=1)}
     js = {k: _jsonable(v) for k, v in res.items()}
     text = json.dumps({k: v.get("summary") for k, v in js.items()}, indent=1)
     print(text)
