@@ -84,3 +84,24 @@ def test_paper_falling_drop_full_run(lbm):
     t, dr = experiments.difference(res)
     early = np.abs(dr[t <= 10000]).max()
     assert early < 0.5                          # nearly no difference up to t = 1e4
+
+
+def test_paper_splash_runs_under_the_forced_form(lbm):
+    """Under the forced order-parameter LBE (f_form = 1) the paper's splash (Re = 480, F_a
+    removed) stays finite to t* = 2 on the GPU, and its diagnostics match the oracle's over the
+    first 500 steps, while the flow develops."""
+    import dataclasses
+    w = W.paper_splash(Re=480.0, steps=3000, remove_Fa=1)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, f_form=1))
+    sim, ref = lbm.Sim.from_workload(w), oracle.Sim.from_workload(w)
+    for _ in range(2):
+        sim.step(250)
+        ref.step(250)
+        dg, dr = sim.diagnostics(), ref.diagnostics()
+        assert dg["finite"] and dr["finite"]
+        for k in ("centroid_x", "centroid_y", "liquid_area", "spread_radius"):
+            assert dg[k] == pytest.approx(dr[k], rel=1e-4), k
+        assert dg["max_u"] == pytest.approx(dr["max_u"], rel=1e-3)
+    sim.step(2500)
+    d = sim.diagnostics()
+    assert d["finite"] and d["max_u"] < 0.3
