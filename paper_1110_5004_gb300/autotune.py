@@ -1,9 +1,13 @@
 """Tile-shape autotuner for the fused step kernel and the batch kernel.
 
 The step kernel's shape is (threads per CTA, rows per CTA).  Threads fix the strip width
-(threads - 6 interior columns); rows trade pipeline warm-up (5 extra S0 rows per segment) for
-parallelism (one CTA per strip x segment).  The best pair depends on the grid, the storage and
-the device, so it is measured: each candidate runs a few steps timed with CUDA events on the
+(threads - 6 interior columns); rows trade pipeline fill (a segment of h rows runs h + 8 row
+iterations, the first and last few with stages idle) for parallelism (one CTA per strip x
+segment).  The kernel is bound by instruction issue, so a step lasts as long as the SM with the
+most CTAs: besides a fixed list of heights, the candidates include, for k = 1..8 resident CTAs
+per SM, the shortest height whose CTA count still fits k x SMs (one row less can add a nearly
+empty wave).  The best pair depends on the grid, the storage and the device, so it is
+measured: each candidate runs about a millisecond of steps timed with CUDA events on the
 simulation's stream, and the fastest is cached per (device, grid class, storage, kernel source)
 in a JSON file next to the library (git-ignored).
 """
@@ -17,7 +21,8 @@ import threading
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(HERE, "_autotune_cache.json")
 THREADS = (64, 128, 256)
-ROWS = (0, 1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 128)
+ROWS = (1, 2, 4, 8, 12, 16, 24, 32, 48, 64, 128)
+MAX_CTAS_PER_SM = 8
 _lock = threading.Lock()
 
 
@@ -62,7 +67,7 @@ def _store(cache):
 
 
 def _key(kind, nx, ny, storage):
-    return "|".join((kind, _device_name(), _kernel_hash(), grid_class(nx, ny), "st%d" % storage))
+    return "|".join((kind, _device_name(), _kernel_hash(), grid_class(nx, ny), "st%d" % storage, "c2"))
 
 
 def _time(fn, reps, stream):
@@ -78,10 +83,47 @@ def _time(fn, reps, stream):
     return a.elapsed_time(b) / reps
 
 
-def tune_sim(sim, reps=6, candidates=None, use_cache=True):
+def _sm_count():
+    import torch
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
+def balanced_rows(nx, ny, threads, sms, max_per_sm=MAX_CTAS_PER_SM):
+    """For each k = 1..max_per_sm, the shortest height h whose CTA count strips x ceil(ny / h)
+    is at most k x sms (the strip count follows the library's rule: strips of at most
+    threads - 6 columns)."""
+    strips = -(-nx // (threads - 6))
+    out = []
+    for k in range(1, max_per_sm + 1):
+        segs = (k * sms) // strips
+        if segs < 1:
+            continue
+        h = -(-ny // segs)
+        if h not in out:
+            out.append(h)
+    return out
+
+
+def sim_candidates(nx, ny, sms):
+    """(threads, rows) pairs measured for an nx x ny simulation on a device with `sms` SMs."""
+    out = []
+    for t in THREADS:
+        for r in list(ROWS) + balanced_rows(nx, ny, t, sms):
+            if (t, r) not in out:
+                out.append((t, r))
+    return out
+
+
+def _reps_for(fn, stream, target_ms=1.0, lo=6, hi=400):
+    """Repetitions that make a timed run last about target_ms."""
+    one = _time(fn, 2, stream)
+    return max(lo, min(hi, int(target_ms / max(one, 1e-4))))
+
+
+def tune_sim(sim, reps=None, candidates=None, use_cache=True):
     """Measure tile candidates on `sim` (its state advances; re-initialise it afterwards) and
     set the fastest.  Returns (threads, rows, ms per step).  The cache key includes the
-    simulation's population storage."""
+    simulation's population storage.  `reps` None: about a millisecond of steps per candidate."""
     import torch
     key = _key("sim", sim.nx, sim.ny, int(sim.params.storage))
     with _lock:
@@ -93,9 +135,10 @@ def tune_sim(sim, reps=6, candidates=None, use_cache=True):
     stream = torch.cuda.current_stream()
     sim.set_stream(stream)
     best = None
-    for t, r in candidates or [(t, r) for t in THREADS for r in ROWS]:
+    for t, r in candidates or sim_candidates(sim.nx, sim.ny, _sm_count()):
         sim.set_tile(t, r)
-        ms = _time(lambda: sim.step(1), reps, stream)
+        n = reps if reps else _reps_for(lambda: sim.step(1), stream)
+        ms = _time(lambda: sim.step(1), n, stream)
         if best is None or ms < best[2]:
             best = (t, r, ms)
     sim.set_tile(best[0], best[1])

@@ -68,7 +68,9 @@ void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, in
   *n_strips = ns;
   *tile_w = (nx + ns - 1) / ns;
   if (seg_h <= 0) {
-    const int segs = slots > ns ? (slots + ns - 1) / ns : 1;
+    // as many segments as fit in one wave of `slots` resident CTAs: the step is issue-bound and
+    // lasts as long as the busiest SM, so a count just above the slots adds a nearly empty wave
+    const int segs = slots >= ns ? slots / ns : 1;
     seg_h = (ny + segs - 1) / segs;
     if (seg_h < 8) seg_h = 8;
   }

@@ -22,6 +22,7 @@ def autotune(monkeypatch, tmp_path):
     monkeypatch.setattr(torch.cuda, "current_stream", lambda *a, **k: None)
     monkeypatch.setattr(at, "CACHE", str(tmp_path / "cache.json"))
     monkeypatch.setattr(at, "_device_name", lambda: "dev")
+    monkeypatch.setattr(at, "_sm_count", lambda: 152)
     return at
 
 
@@ -70,3 +71,26 @@ def test_sim_tuner_caches_per_storage(autotune, monkeypatch):
     c = autotune.tune_sim(FakeSim(1))
     assert len(calls) == 2 * n0 and tuple(c[:2]) == tuple(b[:2])   # then taken from the cache
     assert tuple(a[:2]) == (autotune.THREADS[0], autotune.ROWS[0])
+
+
+@pytest.mark.parametrize("nx,ny,threads,sms", [(2048, 512, 128, 152), (2048, 512, 256, 152), (4096, 4096, 256, 152),
+                                               (128, 128, 128, 152), (300, 77, 64, 10)])
+def test_balanced_rows_fill_whole_waves(autotune, nx, ny, threads, sms):
+    """Each balanced height is the shortest whose CTA count fits k resident CTAs per SM: one row
+    less would exceed k x sms."""
+    strips = -(-nx // (threads - 6))
+    ctas = lambda h: strips * -(-ny // h)
+    hs = autotune.balanced_rows(nx, ny, threads, sms)
+    assert hs and len(set(hs)) == len(hs)
+    for h in hs:
+        k = next(k for k in range(1, autotune.MAX_CTAS_PER_SM + 1) if ctas(h) <= k * sms)
+        assert h == 1 or ctas(h - 1) > k * sms
+
+
+def test_sim_candidates_on_the_splash_grid(autotune):
+    """On 2048 x 512 with 152 SMs the candidates include the one-wave heights measured fastest
+    (128 x 15: 595 CTAs for 608 slots; 128 x 20: 442 CTAs, three per SM), never a zero height
+    (which the library reads as 'keep the current one'), and no duplicates."""
+    c = autotune.sim_candidates(2048, 512, 152)
+    assert (128, 15) in c and (128, 20) in c and (256, 16) in c
+    assert all(r >= 1 for _, r in c) and len(set(c)) == len(c)
