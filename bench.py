@@ -287,7 +287,7 @@ def other_grids(lbm, torch, peak):
                                  ("c1", W.static_droplet(), 400, "L2-resident"),
                                  ("c2", W.falling_droplet(), 40, "L2-resident; re-initialised before timing")):
         sim = lbm.Sim.from_workload(w, stream=stream)
-        t_, r_, _ = autotune.tune_sim(sim, reps=3)
+        t_, r_, _ = autotune.tune_sim(sim)
         sim.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
         sim.step(3)
         torch.cuda.synchronize()
