@@ -1,6 +1,7 @@
 // Ragged batches: many independent simulations (any sizes and parameters) advanced by one
-// persistent launch per time step over a work list of (simulation, strip, segment) tiles.
-// k steps are captured once as a CUDA graph of k launches and replayed while the membership is
+// persistent launch per time step over a work list of (simulation, strip, segment) tiles; two
+// launches when some members use the direct mass defect (its tiles run in their own kernel
+// instance).  k steps are captured once as a CUDA graph and replayed while the membership is
 // unchanged.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel
 // (every operation an explicit round-to-nearest intrinsic), so a member's state is bitwise the
 // same alone or inside any mix.
@@ -22,8 +23,10 @@ struct SimDesc {
   int pad;
 };
 
-// ANY_SD: some member uses the direct mass defect; only then is that tile body compiled in.
-template <int NT, bool ANY_SD>
+// SD: the work list holds the tiles of members that use the direct mass defect (s_form 1), and
+// only that tile body is compiled in.  One function holding both bodies (each for three
+// storages) did not fit 128 registers: it spilled 1.2 KB per thread and ran a third slower.
+template <int NT, bool SD>
 __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
                                               int n_work, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -35,19 +38,11 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
     const bool odd = ((d.cur0 + parity) & 1) != 0;
     g.src = odd ? d.buf1 : d.buf0;
     g.dst = odd ? const_cast<void*>(d.buf0) : d.buf1;
-    // members may differ in storage and mass-defect form; the branches are uniform per tile
-    if (ANY_SD && d.P.s_direct) {
-      switch (g.storage) {
-        case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-        case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-        default: run_tile<NT, MODE_STEP, ST_FP32, true>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      }
-    } else {
-      switch (g.storage) {
-        case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-        case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-        default: run_tile<NT, MODE_STEP, ST_FP32, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      }
+    // members may differ in storage; the branch is uniform per tile
+    switch (g.storage) {
+      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      default: run_tile<NT, MODE_STEP, ST_FP32, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
     }
     __syncthreads();  // shared rings are reused by the next tile
   }
@@ -92,9 +87,9 @@ struct lbm_batch {
   int4* d_work = nullptr;
   size_t cap_sims = 0, cap_work = 0;
   int n_work = 0;
-  int grid = 0;
+  int n_plain = 0;                     // work[0, n_plain): members without the direct mass defect
+  int grid_plain = 0, grid_sd = 0;     // persistent grid of each launch
   int flip = 0;                        // parity offset of every member since the last rebuild
-  bool any_sd = false;                 // some member uses the direct mass defect
   std::map<int, cudaGraphExec_t> graphs;  // 2k + flip -> executable graph for the membership
 };
 
@@ -109,8 +104,9 @@ static int rebuild(lbm_batch* b) {
   std::vector<int> members;
   for (size_t i = 0; i < b->slots.size(); ++i)
     if (b->slots[i]) members.push_back((int)i);
-  // interleave the members' tiles so concurrent CTAs spread over simulations
-  std::vector<std::vector<int4>> per;
+  // interleave the members' tiles so concurrent CTAs spread over simulations; the tiles of
+  // members with the direct mass defect follow those of the others (a launch of their own)
+  std::vector<std::vector<int4>> per[2];
   for (size_t m = 0; m < members.size(); ++m) {
     lbm_sim* s = b->slots[members[m]];
     SimDesc d{};
@@ -127,13 +123,17 @@ static int rebuild(lbm_batch* b) {
     const int nseg = (s->ny + g.seg_h - 1) / g.seg_h;
     for (int sg = 0; sg < nseg; ++sg)
       for (int st = 0; st < g.n_strips; ++st) tl.push_back(make_int4((int)m, st, sg, 0));
-    per.push_back(std::move(tl));
+    per[d.P.s_direct ? 1 : 0].push_back(std::move(tl));
   }
-  size_t most = 0;
-  for (auto& v : per) most = std::max(most, v.size());
-  for (size_t k = 0; k < most; ++k)
-    for (auto& v : per)
-      if (k < v.size()) work.push_back(v[k]);
+  int n_plain = 0;
+  for (int part = 0; part < 2; ++part) {
+    size_t most = 0;
+    for (auto& v : per[part]) most = std::max(most, v.size());
+    for (size_t k = 0; k < most; ++k)
+      for (auto& v : per[part])
+        if (k < v.size()) work.push_back(v[k]);
+    if (part == 0) n_plain = (int)work.size();
+  }
   cudaError_t e;
   if (sims.size() > b->cap_sims) {
     cudaFree(b->d_sims);
@@ -160,14 +160,19 @@ static int rebuild(lbm_batch* b) {
   // host vectors die here: make the uploads complete first
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_fail(e, "batch upload sync");
   b->n_work = (int)work.size();
-  int dev = 0, sms = 0, occ = 0;
+  b->n_plain = n_plain;
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  b->any_sd = false;
-  for (const SimDesc& d : sims) b->any_sd |= d.P.s_direct != 0;
-  if ((e = set_batch_attr(b->nt, b->any_sd)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
-  occ = b->any_sd ? batch_occupancy_sd<true>(b->nt) : batch_occupancy_sd<false>(b->nt);
-  b->grid = std::max(1, std::min(b->n_work, sms * std::max(occ, 1)));
+  b->grid_plain = b->grid_sd = 0;
+  if (b->n_plain > 0) {
+    if ((e = set_batch_attr(b->nt, false)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+    b->grid_plain = std::max(1, std::min(b->n_plain, sms * std::max(batch_occupancy_sd<false>(b->nt), 1)));
+  }
+  if (b->n_work > b->n_plain) {
+    if ((e = set_batch_attr(b->nt, true)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+    b->grid_sd = std::max(1, std::min(b->n_work - b->n_plain, sms * std::max(batch_occupancy_sd<true>(b->nt), 1)));
+  }
   b->flip = 0;
   drop_graphs(b);
   b->dirty = false;
@@ -175,16 +180,19 @@ static int rebuild(lbm_batch* b) {
 }
 
 template <bool SD>
-static void launch_batch_sd(lbm_batch* b, int parity, cudaStream_t st) {
+static void launch_part(lbm_batch* b, const int4* work, int n, int grid, int parity, cudaStream_t st) {
   switch (b->nt) {
-    case 64: k_batch<64, SD><<<b->grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
-    case 256: k_batch<256, SD><<<b->grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
-    default: k_batch<128, SD><<<b->grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, b->d_work, b->n_work, parity); break;
+    case 64: k_batch<64, SD><<<grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, work, n, parity); break;
+    case 256: k_batch<256, SD><<<grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, work, n, parity); break;
+    default: k_batch<128, SD><<<grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, work, n, parity); break;
   }
 }
 
+// One time step of every member: the two launches touch disjoint members.
 static cudaError_t launch_batch(lbm_batch* b, int parity, cudaStream_t st) {
-  if (b->any_sd) launch_batch_sd<true>(b, parity, st); else launch_batch_sd<false>(b, parity, st);
+  if (b->n_plain > 0) launch_part<false>(b, b->d_work, b->n_plain, b->grid_plain, parity, st);
+  if (b->n_work > b->n_plain)
+    launch_part<true>(b, b->d_work + b->n_plain, b->n_work - b->n_plain, b->grid_sd, parity, st);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,34 @@ def test_alone_equals_in_mix_bitwise(lbm):
             assert np.array_equal(m[k], a[k]), k
 
 
+@pytest.mark.parametrize("plain", [0, 1])
+def test_direct_defect_members_in_their_own_launch(lbm, plain):
+    """Members with the direct mass defect run in a launch of their own, after the others': with
+    and without plain members, in every storage, each member stays bitwise equal to a run alone."""
+    base = [W.random_small(77, 52, seed=6, bc_y=W.WALL, gravity=1e-5, remove_Fa=1),
+            W.static_droplet(nx=96, ny=64, R=14.0, remove_Fa=1),
+            W.random_small(61, 90, seed=9, bc_x=W.WALL, bc_y=W.WALL, remove_Fa=1)]
+    members = [(direct_defect(w), st) for w, st in zip(base, (0, 1, 2))]
+    if plain:
+        members += [(W.random_small(130, 37, seed=3, bc_y=W.WALL, gravity=1e-5), 2),
+                    (W.static_droplet(nx=64, ny=64, R=12.0), 0)]
+    alone = []
+    for w, st in members:
+        s = lbm.Sim.from_workload(w, storage=st)
+        s.step(17)
+        alone.append(s.moments())
+    b = lbm.Batch()
+    sims = [lbm.Sim.from_workload(w, storage=st) for w, st in members]
+    for s in sims:
+        b.add(s)
+    b.step(6)
+    b.step(11)
+    for s, a in zip(sims, alone):
+        m = s.moments()
+        for k in a:
+            assert np.array_equal(m[k], a[k]), k
+
+
 def test_batch_matches_oracle(lbm):
     w = W.random_small(70, 45, seed=8, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
     b = lbm.Batch()
