@@ -9,8 +9,11 @@ namespace lbm {
 // ------------------------------------------------------------------ fused step / moments
 
 template <int NT, int MODE, int ST, bool SD, bool FF>
-// 512 / NT resident CTAs per SM (16 warps): caps the registers at 128 per thread.
-__global__ void __launch_bounds__(NT, 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
+// Resident CTAs per SM: 8 of 64 threads or 2 of 256 (16 warps, at most 128 registers per thread),
+// 3 of 128 threads (12 warps, at most 168 registers).  Given the room, the 128-thread FP32 step
+// takes 148 registers instead of 128, and on the 2048 x 512 splash its whole-wave tile (20 rows,
+// 442 CTAs) ran 47.1 us per step against 49.2 us for the best tile at 4 CTAs of 128 registers.
+__global__ void __launch_bounds__(NT, NT == 128 ? 3 : 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
   const int strip = blockIdx.x % g.n_strips;
