@@ -193,7 +193,9 @@ LBM_API int lbm_restore(lbm_sim* sim, const void* buf, size_t bytes);
 LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
 
 /* Tile shape of the fused step kernel: threads per CTA (64, 128 or 256; the CTA covers
- * threads - 6 interior columns) and rows per CTA (>= 1).  0 keeps the current value. */
+ * threads - 6 interior columns) and rows per CTA (>= 1).  0 keeps the current value.  A new
+ * simulation has 128 threads and as many rows per CTA as make one wave of resident CTAs
+ * (at least 8 rows). */
 LBM_API int lbm_set_tile(lbm_sim* sim, int threads, int seg_rows);
 
 /* Kernel launches issued by this simulation since creation (step, init, moments,

@@ -110,6 +110,9 @@ class Sim:
             pass
 
     def set_tile(self, threads=0, seg_rows=0):
+        """Tile of the step kernel: threads per CTA (64, 128 or 256) and rows per CTA; 0 keeps
+        the current value of either (a simulation starts with as many rows per CTA as fill one
+        wave of resident CTAs)."""
         _lib.check(lib().lbm_set_tile(self._h, int(threads), int(seg_rows)))
 
     def set_stream(self, stream):
@@ -210,6 +213,8 @@ class Batch:
         _lib.check(lib().lbm_batch_step(self._h, int(k)))
 
     def set_tile(self, threads=0, seg_rows=0):
+        """Tile of the batch kernel for members without their own rows per CTA; 0 keeps the
+        current value of either."""
         _lib.check(lib().lbm_batch_set_tile(self._h, int(threads), int(seg_rows)))
 
     @property

@@ -25,7 +25,7 @@ struct lbm_sim {
   long long steps = 0;
   long long launches = 0;
   int nt = 128;                        // threads per CTA of the step kernel
-  int seg_h = 0;                       // rows per CTA (0: chosen to fill the GPU)
+  int seg_h = 0;                       // rows per CTA (0: one wave of resident CTAs)
   int sms = 0;                         // multiprocessors of the device
   int occ = 0;                         // resident step CTAs per SM at the current nt
   float sf = 1.0f, sg = 1.0f;          // 16-bit storage scales of the f and gbar planes
