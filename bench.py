@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=480, help="oracle steps for the CPU baseline sample (~10 s)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main line only (no batch / serving legs)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage of the main line (16-bit forms keep FP32 arithmetic)")
     ap.add_argument("--batch-sims", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -393,7 +395,8 @@ def run_ours(args):
     w = workload()
     stream = torch.cuda.current_stream()
     tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
-    sim = lbm.Sim.from_workload(w, stream=stream, tile=tile)
+    storage = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
+    sim = lbm.Sim.from_workload(w, stream=stream, tile=tile, storage=storage)
     tile_how = "given"
     if tile is None:
         # tile shape measured on this device (cached per device, grid class and kernel source);
@@ -441,11 +444,13 @@ def run_ours(args):
     value, total = replica_throughput(sum(per_step), w.cells * args.steps, world, device="cuda")
     mean_step = sum(per_step) / len(per_step)
     peak, peak_kind = measured_peaks()
-    achieved = B_MIN_FP32 * w.cells / mean_step / 1e9
-    tr = traffic_per_launch(w.cells)
+    # 16-bit storage halves the populations' bytes; f_0 stays a float (76 B moved per update)
+    b_min = B_MIN_FP32 if storage == 0 else B_MIN_FP32 // 2
+    achieved = b_min * w.cells / mean_step / 1e9
+    tr = traffic_per_launch(w.cells) if storage == 0 else None   # the record is of the FP32 step
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr, "peak_kind": peak_kind,
-                "bytes_per_lu_algorithmic": B_MIN_FP32, "bytes_per_lu_design": 152,
+                "bytes_per_lu_algorithmic": b_min, "bytes_per_lu_design": 152 if storage == 0 else 76,
                 "kernel": "k_tiles<MODE_STEP> (fused gather/moments/mu/forcing/collide/store)"}
 
     # end to end through the C ABI with pinned host buffers: upload the initial fields, advance
@@ -494,7 +499,7 @@ def run_ours(args):
         line = {"metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "grid": [w.nx, w.ny], "cells": w.cells, "storage": "fp32",
+                "config": {"workload": w.name, "grid": [w.nx, w.ny], "cells": w.cells, "storage": args.storage,
                            "l2": "flushed between timed steps (512 MB write, then 512 MB read); inputs 80 MB",
                            "reinit_every": REINIT_EVERY, "tile": list(tile), "tile_choice": tile_how,
                            "parallelism": "replicas" if world > 1 else "single GPU"},
