@@ -152,7 +152,9 @@ LBM_API int lbm_init_fields(lbm_sim* sim, const float* phi0, const float* ux0, c
 LBM_API int lbm_step(lbm_sim* sim, int n);
 
 /* Macroscopic fields of the current state (phi, rho, ux, uy, p; any pointer may be NULL),
- * row-major nx*ny float32 each, host or device.  Synchronises the stream. */
+ * row-major nx*ny float32 each, host or device.  Synchronises the stream.  When nx is a multiple
+ * of 32, device outputs are written by the moment kernel itself; the others are copied from the
+ * simulation's work planes. */
 LBM_API int lbm_moments(lbm_sim* sim, float* phi, float* rho, float* ux, float* uy, float* p);
 
 /* The additional interfacial force of the current state (Eq. 12: F_a = -u [d_t rho + div(rho u)],

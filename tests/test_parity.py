@@ -350,6 +350,34 @@ def test_device_pointers_in_and_out(lbm):
         assert np.array_equal(out[k].cpu().numpy(), h[k]), k
 
 
+@pytest.mark.parametrize("nx", [64, 40])
+def test_moments_into_pinned_host_and_device_buffers(lbm, nx):
+    """With nx a multiple of 32 the moment pass writes device tensors itself (no staging copy);
+    page-locked host buffers, and every target at other widths, are copied from the pitched work
+    planes.  Either way, and with targets of every kind mixed in one call, the fields equal those
+    the copy path delivers into pageable arrays, bitwise."""
+    import torch
+    names = ("phi", "rho", "ux", "uy", "p")
+    w = W.random_small(nx, 24, seed=6, bc_y=W.WALL, remove_Fa=1)
+    s = lbm.Sim.from_workload(w)
+    s.step(25)
+    ref = s.moments()                                   # pageable numpy outputs: copied
+    nan = float("nan")
+    pinned = {k: torch.full((w.ny, w.nx), nan).pin_memory() for k in names}
+    dev = {k: torch.full((w.ny, w.nx), nan, device="cuda") for k in names}
+    s.moments(pinned)
+    s.moments(dev)
+    for k in names:
+        assert np.array_equal(pinned[k].numpy(), ref[k]), ("pinned", k)
+        assert np.array_equal(dev[k].cpu().numpy(), ref[k]), ("device", k)
+    mixed = {"phi": torch.full((w.ny, w.nx), nan).pin_memory(), "rho": np.full((w.ny, w.nx), nan, np.float32),
+             "ux": torch.full((w.ny, w.nx), nan, device="cuda"), "p": torch.full((w.ny, w.nx), nan).pin_memory()}
+    s.moments(mixed)
+    for k, v in mixed.items():
+        got = v if isinstance(v, np.ndarray) else v.cpu().numpy()
+        assert np.array_equal(got, ref[k]), ("mixed", k)
+
+
 def test_zero_steps_and_null_outputs(lbm):
     w = W.random_small(16, 16, seed=1)
     s = lbm.Sim.from_workload(w)
