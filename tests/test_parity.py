@@ -216,6 +216,25 @@ def test_grid_taller_than_a_launch_dimension(lbm):
     assert d["finite"] and abs(d["sum_phi"] - float(ref["phi"].sum())) <= 1e-6 * w.cells
 
 
+@pytest.mark.parametrize("tile", [None, (128, 82)])
+def test_largest_serving_request(lbm, tile):
+    """The largest grid a c5 request draws (1024 x 4096, falling drop between walls, corrected
+    scheme), at full size against the oracle over 5 steps, with the default tile and the
+    whole-wave tile the tuner offers there (9 strips x 50 segments of 82 rows, 3 CTAs per SM)."""
+    w = W.falling_droplet(nx=1024, ny=4096, R=120.0, yc=3400.0, ratio=10.0, remove_Fa=1)
+    _, got, ref = run_both(lbm, w, 5, tile=tile)
+    assert_parity(got, ref, w)
+
+
+def test_large_periodic_grid_on_the_tuned_tile(lbm):
+    """The 4096 x 4096 periodic static drop of the benchmark's large-grid line (2.4 GB of
+    populations, far beyond L2), at full size against the oracle over 3 steps on the tile the
+    tuner picks on GB300 (128 threads x 316 rows: 34 strips x 13 segments)."""
+    w = W.static_droplet(nx=4096, ny=4096, R=600.0)
+    _, got, ref = run_both(lbm, w, 3, tile=(128, 316))
+    assert_parity(got, ref, w)
+
+
 @pytest.mark.parametrize("nx,tile", [(3193, (64, 0)), (14521, (128, 0)), (131, (64, 9)), (250, (64, 9))])
 def test_strip_ending_short_of_a_side_wall(lbm, nx, tile):
     """Side walls with many strips, among them the widths whose second-to-last strip ends 3
