@@ -66,8 +66,11 @@ def _store(cache):
     os.replace(tmp, CACHE)
 
 
+TUNER_VERSION = "whole-waves-1"   # entries measured over another candidate set are not reused
+
+
 def _key(kind, nx, ny, storage):
-    return "|".join((kind, _device_name(), _kernel_hash(), grid_class(nx, ny), "st%d" % storage, "c2"))
+    return "|".join((kind, _device_name(), _kernel_hash(), grid_class(nx, ny), "st%d" % storage, TUNER_VERSION))
 
 
 def _time(fn, reps, stream):

@@ -25,7 +25,8 @@ struct SimDesc {
 
 // SD: the work list holds the tiles of members that use the direct mass defect (s_form 1), and
 // only that tile body is compiled in.  One function holding both bodies (each for three
-// storages) did not fit 128 registers: it spilled 1.2 KB per thread and ran a third slower.
+// storages) did not fit 128 registers: it spilled 1.2 KB per thread, and a batch of s_form 1
+// members ran at 14.5 GLUPS against 18.8 with the instances split.
 template <int NT, bool SD>
 __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
                                               int n_work, int parity) {
