@@ -45,9 +45,12 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default="", help="threads,rows of the step kernel (default: autotuned)")
     ap.add_argument("--e2e-iters", type=int, default=20)
-    ap.add_argument("--cpu-steps", type=int, default=480, help="oracle steps for the CPU baseline sample (~10 s)")
+    ap.add_argument("--cpu-steps", type=int, default=480,
+                    help="oracle steps for the CPU baseline sample on the splash (~10 s); scaled by cells")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--quick", action="store_true", help="main line only (no batch / serving legs)")
+    ap.add_argument("--workload", default="splash", choices=["splash", "large"],
+                    help="main-line workload: the 2048x512 splash, or the 4096x4096 periodic static drop")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage of the main line (16-bit forms keep FP32 arithmetic)")
     ap.add_argument("--batch-sims", type=int, default=256)
@@ -61,8 +64,10 @@ def env_rank():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def workload():
+def workload(name="splash"):
     import workloads as W
+    if name == "large":
+        return W.static_droplet(nx=4096, ny=4096, R=600.0)   # 2.4 GB of populations, far beyond L2
     return W.splash()
 
 
@@ -83,17 +88,18 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def traffic_per_launch(cells):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
-    current kernel source; scaled to this grid by lattice updates."""
+def traffic_per_launch(w):
+    """DRAM bytes per step-kernel launch from the committed ncu summary of this workload, if it was
+    taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_hash") != kernel_hash():
-        return None
-    return d["dram_bytes_per_lu"] * cells
+    for rec in d if isinstance(d, list) else [d]:          # one record per profiled workload
+        if rec.get("kernel_hash") == kernel_hash() and rec.get("workload") == w.name:
+            return rec["dram_bytes_per_lu"] * w.cells
+    return None
 
 
 class ClockSampler:
@@ -348,7 +354,7 @@ def run_reference(args):
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    w = workload()
+    w = workload(args.workload)
     import oracle
     res = []
     s = oracle.Sim.from_workload(w)
@@ -392,7 +398,7 @@ def run_ours(args):
         dist.barrier()
     import paper_1110_5004_gb300 as lbm
 
-    w = workload()
+    w = workload(args.workload)
     stream = torch.cuda.current_stream()
     tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
     storage = {"fp32": 0, "fp16": 1, "bf16": 2}[args.storage]
@@ -447,7 +453,7 @@ def run_ours(args):
     # 16-bit storage halves the populations' bytes; f_0 stays a float (76 B moved per update)
     b_min = B_MIN_FP32 if storage == 0 else B_MIN_FP32 // 2
     achieved = b_min * w.cells / mean_step / 1e9
-    tr = traffic_per_launch(w.cells) if storage == 0 else None   # the record is of the FP32 step
+    tr = traffic_per_launch(w) if storage == 0 else None   # the record is of the FP32 step
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": tr, "peak_kind": peak_kind,
                 "bytes_per_lu_algorithmic": b_min, "bytes_per_lu_design": 152 if storage == 0 else 76,
@@ -482,7 +488,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(w, args.cpu_steps)
+        cpu = cpu_baseline(w, max(REINIT_EVERY, args.cpu_steps * 2048 * 512 // w.cells))
 
     batch = serving = others = st16 = None
     if not args.quick:
@@ -500,7 +506,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "grid": [w.nx, w.ny], "cells": w.cells, "storage": args.storage,
-                           "l2": "flushed between timed steps (512 MB write, then 512 MB read); inputs 80 MB",
+                           "l2": "flushed between timed steps (512 MB write, then 512 MB read); inputs %d MB"
+                                 % round(76 * w.cells / 1e6),
                            "reinit_every": REINIT_EVERY, "tile": list(tile), "tile_choice": tile_how,
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": roofline,

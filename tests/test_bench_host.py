@@ -1,4 +1,7 @@
-"""Host-side logic of the benchmark: the clock record counts only samples from the timed region."""
+"""Host-side logic of the benchmark: the clock record counts only samples from the timed region,
+and the committed DRAM-traffic record applies only to its own workload and kernel source."""
+import json
+
 import bench
 
 
@@ -14,3 +17,16 @@ def test_clock_summary_uses_timed_region_samples():
     assert c.summary()["samples"] == 1
     c.lines = []
     assert c.summary() is None
+
+
+def test_traffic_record_applies_to_its_workload_and_source_only(tmp_path, monkeypatch):
+    rec = {"workload": bench.workload("splash").name, "kernel_hash": bench.kernel_hash(), "dram_bytes_per_lu": 117.5}
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_hash"])
+    splash, large = bench.workload("splash"), bench.workload("large")
+    assert bench.traffic_per_launch(splash) == 117.5 * splash.cells
+    assert bench.traffic_per_launch(large) is None                 # another workload
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "changed")
+    assert bench.traffic_per_launch(splash) is None                # another kernel source
