@@ -144,7 +144,8 @@ LBM_API int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stre
 
 /* Set the state at t = 0 from phi0, ux0, uy0, p0 (nx*ny float32 each, host or device; ux0,
  * uy0 and p0 may be NULL for zero): f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0).
- * Asynchronous for device inputs; host inputs are copied before return. */
+ * Asynchronous for device inputs; host inputs are copied before return, and the initialisation
+ * kernels stay queued on the simulation's stream behind those copies. */
 LBM_API int lbm_init_fields(lbm_sim* sim, const float* phi0, const float* ux0, const float* uy0,
                     const float* p0);
 

@@ -197,7 +197,8 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
       (e = cudaMalloc(&s->buf[1], s->buf_bytes)) != cudaSuccess ||
       (e = cudaMalloc(&s->fields, (size_t)N_FIELDS * s->plane * sizeof(float))) != cudaSuccess ||
       (e = cudaMalloc(&s->red, ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&s->h_diag, sizeof(lbm_diag))) != cudaSuccess) {
+      (e = cudaMallocHost(&s->h_diag, sizeof(lbm_diag))) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming)) != cudaSuccess) {
     rc = cuda_fail(e, "lbm_create allocation");
     lbm_destroy(s);
     return rc;
@@ -215,6 +216,16 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
   return LBM_OK;
 }
 
+// One nx*ny field between a pitched work plane and a caller's packed buffer.  When the pitch
+// equals nx both are one contiguous block, copied as such rather than row by row.
+static cudaError_t copy_field(const lbm_sim* s, float* dst, size_t dpitch, const float* src, size_t spitch,
+                              cudaMemcpyKind kind) {
+  const size_t row = (size_t)s->nx * sizeof(float);
+  if (dpitch == row && spitch == row)
+    return cudaMemcpyAsync(dst, src, row * s->ny, kind, s->stream);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, s->ny, kind, s->stream);
+}
+
 static int upload_field(lbm_sim* s, int k, const float* src) {
   float* dst = s->fields + (long long)k * s->plane;
   cudaError_t e;
@@ -222,8 +233,7 @@ static int upload_field(lbm_sim* s, int k, const float* src) {
     e = cudaMemsetAsync(dst, 0, (size_t)s->plane * sizeof(float), s->stream);
   } else {
     const cudaMemcpyKind kind = is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    e = cudaMemcpy2DAsync(dst, (size_t)s->pitch * sizeof(float), src, (size_t)s->nx * sizeof(float),
-                          (size_t)s->nx * sizeof(float), s->ny, kind, s->stream);
+    e = copy_field(s, dst, (size_t)s->pitch * sizeof(float), src, (size_t)s->nx * sizeof(float), kind);
   }
   return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_init_fields upload");
 }
@@ -235,12 +245,15 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
   if ((rc = upload_field(s, 0, phi0)) || (rc = upload_field(s, 2, ux0)) || (rc = upload_field(s, 3, uy0)) ||
       (rc = upload_field(s, 4, p0)))
     return rc;
-  cudaError_t e = launch_init(s, s->stream);
+  cudaError_t e = cudaEventRecord(s->uploaded, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields record");
+  e = launch_init(s, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields launch");
   s->launches += s->params.s_form ? 3 : 2;
   s->steps = 0;
-  // host inputs must be consumed before return (pageable copies already are; pinned ones not)
-  if (!is_device_ptr(phi0) && (e = cudaStreamSynchronize(s->stream)) != cudaSuccess)
+  // host inputs must be consumed before return (pageable copies already are; pinned ones not):
+  // wait for the copies only, so the initialisation kernels overlap the caller's next launches
+  if (!is_device_ptr(phi0) && (e = cudaEventSynchronize(s->uploaded)) != cudaSuccess)
     return cuda_fail(e, "lbm_init_fields sync");
   return LBM_OK;
 }
@@ -276,9 +289,8 @@ static int copy_out(lbm_sim* s, float* const* outs, int n, const char* what) {
   for (int k = 0; k < n; ++k) {
     if (!outs[k]) continue;
     const cudaMemcpyKind kind = is_device_ptr(outs[k]) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-    cudaError_t e = cudaMemcpy2DAsync(outs[k], (size_t)s->nx * sizeof(float), s->fields + (long long)k * s->plane,
-                                      (size_t)s->pitch * sizeof(float), (size_t)s->nx * sizeof(float), s->ny, kind,
-                                      s->stream);
+    cudaError_t e = copy_field(s, outs[k], (size_t)s->nx * sizeof(float), s->fields + (long long)k * s->plane,
+                               (size_t)s->pitch * sizeof(float), kind);
     if (e != cudaSuccess) return cuda_fail(e, what);
   }
   cudaError_t e = cudaStreamSynchronize(s->stream);
@@ -363,6 +375,7 @@ int lbm_destroy(lbm_sim* s) {
   cudaFree(s->fields);
   cudaFree(s->red);
   if (s->h_diag) cudaFreeHost(s->h_diag);
+  if (s->uploaded) cudaEventDestroy(s->uploaded);
   delete s;
   return LBM_OK;
 }

@@ -22,6 +22,7 @@ struct lbm_sim {
   float* fields = nullptr;             // 6 planes: phi, rho, ux, uy, p, mu (moments and init)
   double* red = nullptr;               // reduction scratch: ny rows x 12 partials + final record
   lbm_diag* h_diag = nullptr;          // pinned host copy of the final record
+  cudaEvent_t uploaded = nullptr;      // recorded after lbm_init_fields' host-to-device copies
   long long steps = 0;
   long long launches = 0;
   int nt = 128;                        // threads per CTA of the step kernel
