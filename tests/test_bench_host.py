@@ -30,3 +30,9 @@ def test_traffic_record_applies_to_its_workload_and_source_only(tmp_path, monkey
     assert bench.traffic_per_launch(large) is None                 # another workload
     monkeypatch.setattr(bench, "kernel_hash", lambda: "changed")
     assert bench.traffic_per_launch(splash) is None                # another kernel source
+    # the committed form: one record per profiled workload
+    big = dict(rec, workload=large.name, dram_bytes_per_lu=150.8)
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps([rec, big]))
+    monkeypatch.setattr(bench, "kernel_hash", lambda: rec["kernel_hash"])
+    assert bench.traffic_per_launch(splash) == 117.5 * splash.cells
+    assert bench.traffic_per_launch(large) == 150.8 * large.cells
