@@ -218,13 +218,16 @@ LBM_API const char* lbm_last_error(void);
  * synchronisation of a fresh allocation.  It allocates nothing: the per-row partial sums live
  * in one fixed file-scope device array of the library (8192 rows x 12 doubles plus the result,
  * 768 KB, held by every GPU that loads the library until the process exits).
- *   phi, ux, uy, p  device pointers, row-major nx*ny float32 each (caller-owned, read only);
+ *   phi, ux, uy, p  row-major nx*ny float32 each (caller-owned, read only), in device memory of
+ *                   the current device or in managed memory (anything else: LBM_ERR_INVALID_ARG);
  *   ny <= 8192 (larger grids: LBM_ERR_INVALID_ARG with a message), nx >= 1, phi_star > 0;
  *   step            copied into out->step;
  *   cuda_stream     stream the two reduction kernels run on (NULL: legacy default stream);
  *   out             host or device lbm_diag; a host record is filled before return (the stream
  *                   is synchronised) and LBM_ERR_DIVERGED is returned if the fields are not
- *                   finite; a device record is written asynchronously.
+ *                   finite; a device record is written asynchronously.  Synchronising is not
+ *                   possible on a stream under capture: there a host out is refused with
+ *                   LBM_ERR_INVALID_ARG, and a device out must be passed.
  * The reduction is the one lbm_diagnostics performs (same partials, order and result).  The
  * first call on a device looks up the array's device address with that device current; make
  * that first call before any stream capture.  All calls share the array: nothing in it has to

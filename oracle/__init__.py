@@ -43,12 +43,19 @@ class Diag(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+# -O3 with OpenMP over rows.  No -march=native: the oracle must give the same FP64 results on
+# every host it runs on (x86_64 and aarch64), and no contraction into fused multiply-adds, which
+# aarch64 compilers otherwise apply and x86_64 baseline code does not.
+CFLAGS = ["-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp"]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into a shared object next to its source (gcc, OpenMP)."""
     with _lock:
-        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        stamp = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.abspath(__file__)))
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < stamp:
             tmp = _LIB + ".tmp%d" % os.getpid()
-            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+            cmd = ["gcc"] + CFLAGS + ["-o", tmp, _SRC, "-lm"]
             subprocess.run(cmd, check=True)
             os.replace(tmp, _LIB)
     return _LIB

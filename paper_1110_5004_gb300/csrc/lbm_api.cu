@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <initializer_list>
 #include <new>
 #include <string>
 
@@ -252,8 +253,11 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
   s->launches += s->params.s_form ? 3 : 2;
   s->steps = 0;
   // host inputs must be consumed before return (pageable copies already are; pinned ones not):
-  // wait for the copies only, so the initialisation kernels overlap the caller's next launches
-  if (!is_device_ptr(phi0) && (e = cudaEventSynchronize(s->uploaded)) != cudaSuccess)
+  // wait for the copies only, so the initialisation kernels overlap the caller's next launches.
+  // Any one host input is enough to wait: phi0 may be on the device while ux0 is pinned.
+  bool host_input = false;
+  for (const float* in : {phi0, ux0, uy0, p0}) host_input = host_input || (in && !is_device_ptr(in));
+  if (host_input && (e = cudaEventSynchronize(s->uploaded)) != cudaSuccess)
     return cuda_fail(e, "lbm_init_fields sync");
   return LBM_OK;
 }

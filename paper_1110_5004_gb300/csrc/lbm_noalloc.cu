@@ -138,13 +138,15 @@ static int noalloc_scratch(double** out) {
   return LBM_OK;
 }
 
-static bool on_device(const void* p) {
+// Memory the current device's kernels can address: managed memory, or device memory of this
+// device (a field on another GPU would need peer access the library does not set up).
+static bool on_device(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return a.type == cudaMemoryTypeManaged || (a.type == cudaMemoryTypeDevice && a.device == dev);
 }
 
 }  // namespace lbm
@@ -161,19 +163,32 @@ extern "C" int lbm_diagnostics_fields_noalloc(const float* phi, const float* ux,
     return LBM_ERR_INVALID_ARG;
   }
   if (!(phi_star > 0)) return set_error("phi_star must be positive"), LBM_ERR_INVALID_ARG;
-  if (!on_device(phi) || !on_device(ux) || !on_device(uy) || !on_device(p))
-    return set_error("lbm_diagnostics_fields_noalloc: fields must be device memory"), LBM_ERR_INVALID_ARG;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_diagnostics_fields_noalloc: cudaGetDevice");
+  if (!on_device(phi, dev) || !on_device(ux, dev) || !on_device(uy, dev) || !on_device(p, dev))
+    return set_error("lbm_diagnostics_fields_noalloc: fields must be memory of the current device"),
+           LBM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  const bool host_out = !on_device(out, dev);
+  if (host_out) {
+    // a host record needs a stream synchronisation, which a stream under capture refuses
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess)
+      return cuda_fail(e, "lbm_diagnostics_fields_noalloc: cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)
+      return set_error("lbm_diagnostics_fields_noalloc: a host out cannot be filled on a capturing stream; "
+                       "pass a device out"), LBM_ERR_INVALID_ARG;
+  }
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   double* record = scratch + (long long)NOALLOC_MAX_ROWS * DIAG_PARTIALS;
   k_noalloc_rows<<<ny, NOALLOC_T, 0, st>>>(phi_star, nx, ny, phi, ux, uy, p, scratch);
-  cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "lbm_diagnostics_fields_noalloc: row kernel");
   k_noalloc_final<<<1, NOALLOC_T, 0, st>>>(ny, scratch, record, step);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "lbm_diagnostics_fields_noalloc: final kernel");
-  const bool host_out = !on_device(out);
   e = cudaMemcpyAsync(out, record, sizeof(lbm_diag), host_out ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
   if (e == cudaSuccess && host_out) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_diagnostics_fields_noalloc: result copy");

@@ -706,3 +706,52 @@ def test_mass_defect_matches_finite_differences(ch):
     scale = np.abs(sdef).max()
     assert scale > 1e-7
     assert np.abs(fd - sdef).max() < 0.05 * scale
+
+# ----------------------------------------------------------------- pressure closure
+
+
+@pytest.mark.parametrize("remove_Fa", [0, 1])
+def test_pressure_closure_relaxation_is_tau_independent(remove_Fa):
+    """Pin of the pressure closure p = sum gbar + cs2 u.grad(rho) / 2 (the second-order scheme of
+    Eq. 8 with the u.grad(p) term dropped after Eq. 10).
+
+    The pressure distribution of the text before Eq. 6, g_a = cs2 f_a + psi w_a, has p = sum g_a,
+    and g^eq carries the same zeroth moment p; the relaxation therefore conserves the zeroth
+    moment of g whatever tau is.  With gbar = g - S/2 and sum S = -u.grad(psi) (pinned by
+    test_forcing_moments) the exact pressure is p = sum gbar - u.grad(psi)/2.  Dropping the
+    u.grad(p) part of it, as the paper does for incompressible flows, leaves exactly one
+    tau-dependent term in the collision: on one and the same state, relaxed once with tau_1 and
+    once with tau_2,
+        sum_a gbar*_a(tau_1) - sum_a gbar*_a(tau_2) = (1/tau_1 - 1/tau_2) u.grad(p) / 2.
+    The state has a drop at density ratio 10 moving through a smooth random velocity field, so
+    u.grad(rho) is large across the interface: a flipped sign or a lost factor in the
+    cs2 u.grad(rho) / 2 term adds (1/tau_1 - 1/tau_2) times a multiple of cs2 u.grad(rho) to the
+    left side, far above the tolerance.  grad(p) is the test's own isotropic stencil."""
+    tau1, tau2 = 0.7, 1.3
+    nu1, nu2 = (tau1 - 0.5) / 3.0, (tau2 - 0.5) / 3.0
+    w1 = W.random_small(48, 40, seed=52, ratio=10.0, u_amp=0.02, nu_A=nu1, nu_B=nu1, remove_Fa=remove_Fa)
+    s1 = oracle.Sim.from_workload(w1)
+    s1.step(20)
+    f, g = s1.get_state()
+    m = s1.moments()
+    w2 = dataclasses.replace(w1, phys=dataclasses.replace(w1.phys, nu_A=nu2, nu_B=nu2))
+    s2 = oracle.Sim.from_workload(w2)
+    s2.set_state(f, g)
+    m2 = s2.moments()
+    for k in m:   # u and p do not depend on tau_g
+        np.testing.assert_array_equal(m2[k], m[k])
+    np.testing.assert_allclose(s1.field(oracle.TAU_G), tau1, rtol=1e-14)
+    np.testing.assert_allclose(s2.field(oracle.TAU_G), tau2, rtol=1e-14)
+    _, gst1 = s1.collide()
+    _, gst2 = s2.collide()
+    lhs = gst1.sum(0) - gst2.sum(0)
+    gpx, gpy = iso_grad_periodic(m["p"])
+    d_omega = 1.0 / tau1 - 1.0 / tau2
+    rhs = 0.5 * d_omega * (m["ux"] * gpx + m["uy"] * gpy)
+    np.testing.assert_allclose(lhs, rhs, rtol=0, atol=2e-16)
+    # the state exercises the closure: a sign or factor error in its cs2 u.grad(rho) / 2 term
+    # would move the left side by at least this much somewhere
+    grx, gry = iso_grad_periodic(m["rho"])
+    probe = np.abs(0.5 * d_omega * CS2 * (m["ux"] * grx + m["uy"] * gry)).max()
+    assert probe > 1e3 * 2e-16, probe
+    assert probe > 10 * np.abs(rhs).max(), (probe, np.abs(rhs).max())

@@ -48,12 +48,14 @@ def test_static_droplet_1000_steps(lbm, name, st):
     assert (dg["p_liquid"] - dg["p_gas"]) == pytest.approx(dr["p_liquid"] - dr["p_gas"], rel=2e-2)
 
 
-@pytest.mark.parametrize("name,st,vel_tol,phi_tol", [("fp16", 1, 5e-3, 1e-3), ("bf16", 2, 6e-2, 3e-2)])
-def test_falling_droplet_centroid_velocity(lbm, name, st, vel_tol, phi_tol):
-    """A falling droplet (rho 1:0.1, walls on y) for 1500 steps.  FP16 meets the bounds (phi
-    within 1e-3, centroid velocity within 0.5 %).  BF16 does not: its 8-bit mantissa cannot
-    resolve the velocity carried by differences of populations (measured 3.8 % off in velocity,
-    1.6 % in phi); its looser bounds here only guard that finding against regressions."""
+BF16_SHORTFALL = ("BF16 storage misses the reduced-storage bound on a falling drop: its 8-bit "
+                  "mantissa cannot resolve the velocity carried by differences of populations "
+                  "(measured 3.8 % off in centroid velocity, 1.6 % in phi)")
+
+
+def falling_drop_errors(lbm, st):
+    """A falling droplet (rho 1:0.1, walls on y) for 1500 steps against the FP64 oracle:
+    relative centroid-velocity error, relative L-inf on phi, relative total-phi difference."""
     w = W.falling_droplet(nx=96, ny=200, R=16.0, yc=140.0, ratio=10.0, gravity=5e-6, nu_A=0.1,
                           visc_ratio=1.0, steps=0)
     sim = lbm.Sim.from_workload(w, storage=st)
@@ -62,9 +64,29 @@ def test_falling_droplet_centroid_velocity(lbm, name, st, vel_tol, phi_tol):
     ref.step(1500)
     dg, dr = sim.diagnostics(), ref.diagnostics()
     assert dr["vel_y"] < -1e-4                         # it does fall
-    assert dg["vel_y"] == pytest.approx(dr["vel_y"], rel=vel_tol)
-    assert rel_linf(sim.moments()["phi"], ref.moments()["phi"]) <= phi_tol
-    assert abs(dg["sum_phi"] - dr["sum_phi"]) <= 5e-3 * abs(dr["sum_phi"])
+    return (abs(dg["vel_y"] - dr["vel_y"]) / abs(dr["vel_y"]),
+            rel_linf(sim.moments()["phi"], ref.moments()["phi"]),
+            abs(dg["sum_phi"] - dr["sum_phi"]) / abs(dr["sum_phi"]))
+
+
+@pytest.mark.parametrize("name,st", [("fp16", 1), pytest.param("bf16", 2, marks=pytest.mark.xfail(
+    strict=True, reason=BF16_SHORTFALL))])
+def test_falling_droplet_centroid_velocity(lbm, name, st):
+    """The stated reduced-storage bounds: phi within 1e-3, centroid velocity and total phi within
+    0.5 %.  FP16 meets them; BF16 is expected to fail (strict: a pass would flag a change)."""
+    vel, phi, mass = falling_drop_errors(lbm, st)
+    assert vel <= 5e-3, vel
+    assert phi <= 1e-3, phi
+    assert mass <= 5e-3, mass
+
+
+def test_bf16_known_shortfall_stays_as_measured(lbm):
+    """BF16's documented shortfall on the falling drop, held where it was measured so that a
+    regression shows: centroid velocity within 6 % and phi within 3e-2 of the oracle."""
+    vel, phi, mass = falling_drop_errors(lbm, 2)
+    assert vel <= 6e-2, vel
+    assert phi <= 3e-2, phi
+    assert mass <= 5e-3, mass
 
 
 @pytest.mark.parametrize("name,st", STORAGES)
