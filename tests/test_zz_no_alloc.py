@@ -87,7 +87,7 @@ def test_noalloc_device_record_on_a_side_stream_twice(lbm):
         rc = L.lbm_diagnostics_fields_noalloc(
             fields["phi"].data_ptr(), fields["ux"].data_ptr(), fields["uy"].data_ptr(), fields["p"].data_ptr(),
             w.nx, w.ny, w.phys.phi_star, sim.step_count, side.cuda_stream,
-            ctypes.c_void_p(recs[call].data_ptr()))
+            ctypes.cast(recs[call].data_ptr(), ctypes.POINTER(_lib.lbm_diag)))
         assert rc == 0, L.lbm_last_error()
         keep.append(fields)
     side.synchronize()
