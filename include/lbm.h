@@ -136,8 +136,9 @@ LBM_API size_t lbm_device_bytes(int nx, int ny, int storage);
 /* Device bytes held by an existing simulation (lbm_device_bytes plus the s_form = 1 planes). */
 LBM_API size_t lbm_sim_device_bytes(const lbm_sim* sim);
 
-/* Create a simulation on the current CUDA device.  nx, ny >= 3 (>= 4 along a walled axis);
- * parameters are validated (tau > 1/2, densities, beta, kappa, phi* > 0, theta_M >= 0).
+/* Create a simulation on the current CUDA device.  nx, ny >= 3 (>= 4 along a walled axis),
+ * and ny * pitch * 76 B < 2 GiB (pitch = nx rounded up to 32: about 28 M cells); parameters
+ * are validated (tau > 1/2, densities, beta, kappa, phi* > 0, theta_M >= 0).
  * cuda_stream: a cudaStream_t (may be NULL).  On success *out owns cudaMalloc'd state.
  * Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM (device allocation failed), LBM_ERR_CUDA. */
 LBM_API int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out);
@@ -178,8 +179,13 @@ LBM_API long long lbm_step_count(const lbm_sim* sim);
 
 /* Checkpoint / resume (no counterpart in the paper: it lets a server evict a simulation's
  * device state to host memory and resume it later bitwise).  A checkpoint is a 64-byte header
- * (magic "LBMC", version 1, nx, ny, row pitch, storage, step count, payload size) followed by
- * the raw population buffer of the current state; it holds no parameters.
+ * (magic "LBMC", version 2, nx, ny, row pitch, storage, step count, payload size) followed by
+ * the raw population buffer of the current state; it holds no parameters.  Version 2 is the
+ * blocked population layout: each row is pitch / 32 blocks of 32 cells, a block holding every
+ * population plane of its cells in turn (FP32: f_0..f_8, gbar_0..gbar_8, f_0lo, 128 B each;
+ * 16-bit: the FP32 rest plane, then 17 planes of 64 B); with s_form = 1 two FP32 planes
+ * [rho, div(rho u)] of ny rows x pitch follow the populations.  Version 1 checkpoints (plain
+ * planes) are rejected.
  * lbm_checkpoint_bytes: size of the checkpoint of `sim` (0 if sim is NULL).
  * lbm_checkpoint: writes it to `buf` (host or device memory, at least checkpoint_bytes long,
  *   caller-owned); synchronous.  A batch member must be removed from its batch first.

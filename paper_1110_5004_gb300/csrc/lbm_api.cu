@@ -83,6 +83,7 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
   g.src = src;
   g.dst = dst;
   g.plane = (int)s->plane;
+  g.row_bytes = s->pitch / BLK * block_bytes(s->params.storage);
   g.storage = s->params.storage;
   g.sf = s->sf;
   g.isf = 1.0f / s->sf;
@@ -115,8 +116,9 @@ static int check_params(int nx, int ny, const lbm_params* p) {
     return set_error("bc_x/bc_y must be LBM_PERIODIC or LBM_WALL"), LBM_ERR_INVALID_ARG;
   if (nx < (p->bc_x == LBM_WALL ? 4 : 3) || ny < (p->bc_y == LBM_WALL ? 4 : 3))
     return set_error("grid %dx%d too small (>= 3, >= 4 along a walled axis)", nx, ny), LBM_ERR_INVALID_ARG;
-  if ((long long)ny * pitch_of(nx) >= (1LL << 31) / N_PLANES)
-    return set_error("grid %dx%d too large", nx, ny), LBM_ERR_INVALID_ARG;
+  // byte offsets inside one population buffer are 32-bit (76 B per cell in FP32: 28 M cells)
+  if ((long long)ny * pitch_of(nx) * state_bytes_per_cell(LBM_FP32) >= (1LL << 31))
+    return set_error("grid %dx%d too large (one state buffer must stay below 2 GiB)", nx, ny), LBM_ERR_INVALID_ARG;
   if (!(p->tau_f > 0.5 && p->tau_g_A > 0.5 && p->tau_g_B > 0.5))
     return set_error("relaxation times must exceed 1/2"), LBM_ERR_INVALID_ARG;
   if (!(p->rho_A > 0 && p->rho_B > 0)) return set_error("densities must be positive"), LBM_ERR_INVALID_ARG;
@@ -391,7 +393,7 @@ long long lbm_step_count(const lbm_sim* s) { return s ? s->steps : -1; }
 namespace {
 struct CkptHeader {
   uint32_t magic;       // "LBMC"
-  uint32_t version;     // 1
+  uint32_t version;     // 2: blocked population layout (32-cell blocks)
   int32_t nx, ny, pitch, storage;
   int64_t steps;
   uint64_t payload;     // bytes of the population buffer that follows
@@ -399,6 +401,7 @@ struct CkptHeader {
 };
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 constexpr uint32_t CKPT_MAGIC = 0x434d424cu;   // "LBMC" little-endian
+constexpr uint32_t CKPT_VERSION = 2;
 
 size_t payload_bytes(const lbm_sim* s) { return s->buf_bytes; }
 }  // namespace
@@ -415,7 +418,7 @@ int lbm_checkpoint(lbm_sim* s, void* buf, size_t bytes) {
     return set_error("checkpoint buffer of %zu bytes, %zu needed", bytes, lbm_checkpoint_bytes(s)), LBM_ERR_INVALID_ARG;
   CkptHeader h{};
   h.magic = CKPT_MAGIC;
-  h.version = 1;
+  h.version = CKPT_VERSION;
   h.nx = s->nx;
   h.ny = s->ny;
   h.pitch = s->pitch;
@@ -442,7 +445,7 @@ int lbm_restore(lbm_sim* s, const void* buf, size_t bytes) {
   cudaError_t e = cudaMemcpyAsync(&h, buf, sizeof(h), dev ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_restore header");
-  if (h.magic != CKPT_MAGIC || h.version != 1) return set_error("not a checkpoint (bad magic or version)"), LBM_ERR_INVALID_ARG;
+  if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) return set_error("not a checkpoint (bad magic or version)"), LBM_ERR_INVALID_ARG;
   if (h.nx != s->nx || h.ny != s->ny || h.pitch != s->pitch || h.storage != s->params.storage ||
       h.payload != payload_bytes(s))
     return set_error("checkpoint of a %dx%d storage-%d grid, simulation is %dx%d storage %d", h.nx, h.ny, h.storage,

@@ -1,17 +1,21 @@
 // Device side of the two-distribution D2Q9 multiphase lattice Boltzmann step for sm_103a.
 //
 // State layout in HBM (one simulation, one buffer of a ping-pong pair):
-//   19 planes [f_0..f_8, gbar_0..gbar_8, f_0lo], each ny rows of `pitch` elements (pitch = nx
-//   rounded up to 32 elements, so every row starts on a 128-byte boundary).  The planes hold
-//   POST-collision populations at their source cell; a step pulls f_a(x) = f*_a(x - e_a) (or the
-//   reversed population at a wall), computes the macroscopic fields, collides in registers and
-//   writes f*_a(x) back at x: every global store is an aligned, coalesced row segment.
+//   19 population planes [f_0..f_8, gbar_0..gbar_8, f_0lo], stored in blocks of 32 cells: a row
+//   of the grid is pitch / 32 consecutive blocks (pitch = nx rounded up to 32), and a block holds
+//   the 32 cells' values of every plane, plane after plane (FP32: 19 x 128 B = 2432 B).  The
+//   offset of a plane inside a block is a compile-time constant, so one byte offset per (row,
+//   column) addresses all populations of a cell, and a warp's access to one plane of 32
+//   consecutive cells is one or two aligned 128-byte segments.  The planes hold POST-collision
+//   populations at their source cell; a step pulls f_a(x) = f*_a(x - e_a) (or the reversed
+//   population at a wall), computes the macroscopic fields, collides in registers and writes
+//   f*_a(x) back at x: every global store is an aligned, coalesced segment.
 //   The rest population f_0 ~ phi is the only O(1) population; it is kept as an unevaluated
 //   float pair f_0 + f_0lo (plane 18) so that phi, and through it mu and the surface-tension
 //   force, carry ~2^-48 relative precision with FP32 arithmetic.  All other populations are
 //   O(mu, u) and need no such care.
 //   With the direct mass defect (s_form 1) each buffer also holds, after the populations, two
-//   FP32 planes [rho, div(rho u)] of the step that wrote it.
+//   FP32 planes [rho, div(rho u)] of the step that wrote it, each ny rows of `pitch` elements.
 //
 // The fused step kernel marches a CTA up a strip of columns.  One thread owns one column of the
 // strip plus a 3-column halo on each side, and per row iteration runs four skewed stages whose
@@ -101,10 +105,26 @@ constexpr int ST_FP32 = 0, ST_FP16 = 1, ST_BF16 = 2;
 
 __host__ __device__ constexpr long long state_bytes_per_cell(int st) { return st == ST_FP32 ? 4 * N_PLANES : 4 + 2 * 17; }
 
+// Blocked layout: 32 cells per block.  FP32: 19 planes of 128 B.  16-bit: the FP32 rest plane
+// (128 B), then 17 planes of 64 B.
+constexpr int BLK = 32;
+__host__ __device__ constexpr int block_bytes(int st) { return (int)state_bytes_per_cell(st) * BLK; }
+// Byte offset of plane a inside a block (lane 0).
+template <int ST>
+__host__ __device__ constexpr int plane_off(int a) {
+  return ST == ST_FP32 ? a * BLK * 4 : (a == 0 ? 0 : BLK * 4 + (a - 1) * BLK * 2);
+}
+// Byte offsets of one cell's lane inside the population region: `b4` for 4-byte planes (every
+// plane in FP32; the rest plane in 16-bit storage), `b2` for the 2-byte planes.
+struct CellB {
+  int b4, b2;
+};
+
 struct Grid {
   const void* src;      // post-collision state at t-1 (read)
   void* dst;            // post-collision state at t (write)
-  int plane;            // elements per plane (ny * pitch); all planes fit in 2^31 elements
+  int plane;            // elements per plane of the s_form planes (ny * pitch)
+  int row_bytes;        // bytes per population row: pitch / 32 blocks (the region fits in 2^31 bytes)
   int storage;          // ST_FP32 / ST_FP16 / ST_BF16
   float sf, isf;        // 16-bit scale of the f planes and its inverse
   float sg, isg;        // 16-bit scale of the gbar planes and its inverse
@@ -137,22 +157,36 @@ __device__ __forceinline__ int wrap1(int i, int n) {
   return i < 0 ? i + n : (i >= n ? i - n : i);
 }
 
+// Byte offsets of column x inside a population row.
+template <int ST>
+__host__ __device__ __forceinline__ CellB col_bytes(int x) {
+  const int blk = (x >> 5) * block_bytes(ST), lane = x & (BLK - 1);
+  return CellB{blk + lane * 4, blk + lane * 2};
+}
+__host__ __device__ __forceinline__ CellB cell_at(int row_off, CellB c) { return CellB{row_off + c.b4, row_off + c.b2}; }
+
 // Column part of one thread's pull neighbourhood (fixed for the whole tile).
 struct ColNb {
   int xm, x0, xq;      // physical columns of x-1, x, x+1 (wrapped)
+  CellB cm, c0, cq;    // their byte offsets inside a population row
   bool wl, wr;         // x-1 / x+1 lie beyond a wall
 };
 // Row part of the neighbourhood of one gathered row.
 struct RowNb {
-  int rm, r0, rq;      // element offsets (row * pitch) of rows y-1, y, y+1 (wrapped)
+  int rm, r0, rq;      // element offsets (row * pitch) of rows y-1, y, y+1 (wrapped): s_form planes
+  int bm, b0, bq;      // byte offsets (row * row_bytes) of the same rows in the population region
   bool wb, wt;         // y-1 / y+1 lie beyond a wall
 };
 
+template <int ST>
 __device__ __forceinline__ ColNb make_col(int xp, const Grid& g) {
   ColNb c;
   c.x0 = xp;
   c.xm = xp == 0 ? g.nx - 1 : xp - 1;
   c.xq = xp == g.nx - 1 ? 0 : xp + 1;
+  c.cm = col_bytes<ST>(c.xm);
+  c.c0 = col_bytes<ST>(c.x0);
+  c.cq = col_bytes<ST>(c.xq);
   c.wl = g.bc_x == BC_WALL && xp == 0;
   c.wr = g.bc_x == BC_WALL && xp == g.nx - 1;
   return c;
@@ -163,6 +197,9 @@ __device__ __forceinline__ RowNb make_row(int yp, const Grid& g) {
   r.r0 = yp * g.pitch;
   r.rm = yp == 0 ? (g.ny - 1) * g.pitch : r.r0 - g.pitch;
   r.rq = yp == g.ny - 1 ? 0 : r.r0 + g.pitch;
+  r.b0 = yp * g.row_bytes;
+  r.bm = yp == 0 ? (g.ny - 1) * g.row_bytes : r.b0 - g.row_bytes;
+  r.bq = yp == g.ny - 1 ? 0 : r.b0 + g.row_bytes;
   r.wb = g.bc_y == BC_WALL && yp == 0;
   r.wt = g.bc_y == BC_WALL && yp == g.ny - 1;
   return r;
@@ -175,15 +212,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Population a (0..8 f, 9..17 gbar, 18 f_0lo) at element idx of its plane, as stored bits (a float,
-// or a 16-bit value in the low half), and their decoding.  A prefetch keeps the bits and decodes
-// them where they are used, so that the conversion does not wait for the load at the point of issue.
+// Population a (0..8 f, 9..17 gbar, 18 f_0lo) of the cell at byte offsets c, as stored bits (a
+// float, or a 16-bit value in the low half), and their decoding.  A prefetch keeps the bits and
+// decodes them where they are used, so that the conversion does not wait for the load at the
+// point of issue.
 template <int ST>
-__device__ __forceinline__ unsigned int ld_raw(const void* __restrict__ base, int plane, int a, int idx) {
-  if (ST == ST_FP32) return __float_as_uint(__ldg(static_cast<const float*>(base) + a * plane + idx));
-  if (a == 0) return __float_as_uint(__ldg(static_cast<const float*>(base) + idx));
-  const unsigned short* h = reinterpret_cast<const unsigned short*>(static_cast<const float*>(base) + plane);
-  return __ldg(h + (a - 1) * plane + idx);
+__device__ __forceinline__ unsigned int ld_raw(const void* __restrict__ base, int a, CellB c) {
+  const char* p = static_cast<const char*>(base) + plane_off<ST>(a);
+  if (ST == ST_FP32 || a == 0) return __float_as_uint(__ldg(reinterpret_cast<const float*>(p + c.b4)));
+  return __ldg(reinterpret_cast<const unsigned short*>(p + c.b2));
 }
 
 template <int ST>
@@ -195,16 +232,14 @@ __device__ __forceinline__ float dec_pop(unsigned int raw, int a, float inv_scal
 }
 
 template <int ST>
-__device__ __forceinline__ void st_pop(void* __restrict__ base, int plane, int a, int idx, float v, float scale) {
-  if (ST == ST_FP32) {
-    static_cast<float*>(base)[a * plane + idx] = v;
-  } else if (a == 0) {
-    static_cast<float*>(base)[idx] = v;
+__device__ __forceinline__ void st_pop(void* __restrict__ base, int a, CellB c, float v, float scale) {
+  char* p = static_cast<char*>(base) + plane_off<ST>(a);
+  if (ST == ST_FP32 || a == 0) {
+    *reinterpret_cast<float*>(p + c.b4) = v;
   } else {
-    unsigned short* h = reinterpret_cast<unsigned short*>(static_cast<float*>(base) + plane);
     const float sv = __fmul_rn(v, scale);
-    h[(a - 1) * plane + idx] = ST == ST_FP16 ? __half_as_ushort(__float2half_rn(sv))
-                                             : __bfloat16_as_ushort(__float2bfloat16_rn(sv));
+    *reinterpret_cast<unsigned short*>(p + c.b2) = ST == ST_FP16 ? __half_as_ushort(__float2half_rn(sv))
+                                                                 : __bfloat16_as_ushort(__float2bfloat16_rn(sv));
   }
 }
 
@@ -213,23 +248,22 @@ __device__ __forceinline__ void st_pop(void* __restrict__ base, int plane, int a
 // v[a] = P*_a(x - e_a), or P*_opp(a)(x) when x - e_a lies beyond a wall (half-way bounce-back).
 // Cells with no wall neighbour take the branch-free path.
 template <int ST, int FIRST>
-__device__ __forceinline__ void gather9(const void* __restrict__ src, int plane, const ColNb& c, const RowNb& r,
-                                        unsigned int v[Q]) {
+__device__ __forceinline__ void gather9(const void* __restrict__ src, const ColNb& c, const RowNb& r, unsigned int v[Q]) {
   if (!(c.wl | c.wr | r.wb | r.wt)) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-      const int sx = cx(a) == 1 ? c.xm : (cx(a) == -1 ? c.xq : c.x0);
-      const int sr = cy(a) == 1 ? r.rm : (cy(a) == -1 ? r.rq : r.r0);
-      v[a] = ld_raw<ST>(src, plane, FIRST + a, sr + sx);
+      const CellB sx = cx(a) == 1 ? c.cm : (cx(a) == -1 ? c.cq : c.c0);
+      const int sr = cy(a) == 1 ? r.bm : (cy(a) == -1 ? r.bq : r.b0);
+      v[a] = ld_raw<ST>(src, FIRST + a, cell_at(sr, sx));
     }
   } else {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const int ex = cx(a), ey = cy(a);
       const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && r.wb) || (ey == -1 && r.wt);
-      const int sx = ex == 1 ? c.xm : (ex == -1 ? c.xq : c.x0);
-      const int sr = ey == 1 ? r.rm : (ey == -1 ? r.rq : r.r0);
-      v[a] = hit ? ld_raw<ST>(src, plane, FIRST + opp(a), r.r0 + c.x0) : ld_raw<ST>(src, plane, FIRST + a, sr + sx);
+      const CellB sx = ex == 1 ? c.cm : (ex == -1 ? c.cq : c.c0);
+      const int sr = ey == 1 ? r.bm : (ey == -1 ? r.bq : r.b0);
+      v[a] = hit ? ld_raw<ST>(src, FIRST + opp(a), cell_at(r.b0, c.c0)) : ld_raw<ST>(src, FIRST + a, cell_at(sr, sx));
     }
   }
 }
@@ -312,7 +346,7 @@ struct CollideC {
 
 template <int ST, int A, bool FF>
 __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q], const float gb[Q], const Grid& g,
-                                            int cell, float& fsum, float& ofeqsum) {
+                                            CellB cell, float& fsum, float& ofeqsum) {
   constexpr int C = A == 0 ? 0 : (A <= 4 ? 1 : 2);
   constexpr float w = wgt(A);
   float poly, t1w, t2;
@@ -328,7 +362,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
   }
   const float gmw = fmul(w, poly);
   const float S = fmad(gmw, t2, t1w);
-  st_pop<ST>(g.dst, g.plane, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
+  st_pop<ST>(g.dst, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
   if (A > 0) {
     float ofeq;
     if constexpr (FF) {
@@ -340,7 +374,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
     }
     fsum = fadd(fsum, f[A]);
     ofeqsum = fadd(ofeqsum, ofeq);
-    st_pop<ST>(g.dst, g.plane, A, cell, fmad(k.keep_f, f[A], ofeq), g.sf);
+    st_pop<ST>(g.dst, A, cell, fmad(k.keep_f, f[A], ofeq), g.sf);
   }
 }
 
@@ -350,7 +384,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
 template <int ST, bool FF>
 __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx12, float gpy12,
                                               float phi_hi, float phi_lo, float phiD, const float f[Q],
-                                              const float gb[Q], const Grid& g, int cell) {
+                                              const float gb[Q], const Grid& g, CellB cell) {
   CollideC k;
   k.ux = r.ux;
   k.uy = r.uy;
@@ -421,10 +455,10 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
     two_sum(phi_hi, fadd(fadd(fsub(phi_lo, fsum), fmad(P.omega_f, fsum, -ofeqsum)), phiD), hi, lo);
   }
   if (ST == ST_FP32) {
-    st_pop<ST>(g.dst, g.plane, 0, cell, hi, 1.0f);
-    st_pop<ST>(g.dst, g.plane, PLANE_F0LO, cell, lo, 1.0f);
+    st_pop<ST>(g.dst, 0, cell, hi, 1.0f);
+    st_pop<ST>(g.dst, PLANE_F0LO, cell, lo, 1.0f);
   } else {
-    st_pop<ST>(g.dst, g.plane, 0, cell, fadd(hi, lo), 1.0f);
+    st_pop<ST>(g.dst, 0, cell, fadd(hi, lo), 1.0f);
   }
 }
 
@@ -470,7 +504,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto ghost_slot = [&](int r) { return r == 0 ? slot(-1) : slot(g.ny); };
   auto is_wall_row = [&](int r) { return ywall && (r == 0 || r == g.ny - 1); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
-  const ColNb cn = make_col(xp, g);
+  const ColNb cn = make_col<ST>(xp, g);
   constexpr int USLOT = 2 * NT;
   float* const uring = &sm.urows[0][0][0];
   // Ring slot of row r; the ghost rows beyond a wall (-1, ny) have slots of their own, since a
@@ -526,18 +560,21 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
       rn.r0 = r * g.pitch;
       rn.rm = rn.r0 - g.pitch;
       rn.rq = rn.r0 + g.pitch;
+      rn.b0 = r * g.row_bytes;
+      rn.bm = rn.b0 - g.row_bytes;
+      rn.bq = rn.b0 + g.row_bytes;
       rn.wb = rn.wt = false;
       return rn;
     }
   };
   auto fetch_f = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
-    gather9<ST, 0>(g.src, g.plane, cn, rn, fpr);
-    fpr[Q] = ST == ST_FP32 ? ld_raw<ST>(g.src, g.plane, PLANE_F0LO, rn.r0 + cn.x0) : 0u;
+    gather9<ST, 0>(g.src, cn, rn, fpr);
+    fpr[Q] = ST == ST_FP32 ? ld_raw<ST>(g.src, PLANE_F0LO, cell_at(rn.b0, cn.c0)) : 0u;
   };
   auto fetch_g = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
-    gather9<ST, Q>(g.src, g.plane, cn, rn, gpr);
+    gather9<ST, Q>(g.src, cn, rn, gpr);
     if constexpr (SD) {
       const float* sp = reinterpret_cast<const float*>(static_cast<const char*>(g.src) + g.spoff);
       spr[0] = __float_as_uint(__ldg(sp + rn.r0 + cn.x0));
@@ -756,7 +793,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
           sp[g.plane + r * g.pitch + xp] = fmul(fadd(djx, djy), 1.0f / 12.0f);
         }
         collide_store<ST, FF>(P, prev, q0[0], gpx, gpy, ring[o5 + R_PHI_HI * NT + t], ring[o5 + R_PHI_LO * NT + t], phiD,
-                          f, gb, g, r * g.pitch + xp);
+                          f, gb, g, cell_at(r * g.row_bytes, cn.c0));
       }
     }
     prev = cur;

@@ -130,7 +130,7 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
     const float* uy = fields + 3 * g.plane;
     const float* pp = fields + 4 * g.plane;
     const float* mu = fields + 5 * (long long)g.plane;
-    const long long cell = (long long)y * g.pitch + x;
+    const CellB cell = cell_at(y * g.row_bytes, col_bytes<ST>(x));
   #pragma unroll
     for (int a = 0; a < Q; ++a) {
       int xw = x + cx(a), yw = y + cy(a);
@@ -169,16 +169,15 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
         float hi, lo;
         two_sum(ph, -rest, hi, lo);
         if (ST == ST_FP32) {
-          st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi, 1.0f);
-          st_pop<ST>(g.dst, g.plane, PLANE_F0LO, (int)cell, lo, 1.0f);
+          st_pop<ST>(g.dst, 0, cell, hi, 1.0f);
+          st_pop<ST>(g.dst, PLANE_F0LO, cell, lo, 1.0f);
         } else {
-          st_pop<ST>(g.dst, g.plane, 0, (int)cell, hi + lo, 1.0f);
+          st_pop<ST>(g.dst, 0, cell, hi + lo, 1.0f);
         }
       } else {
-        st_pop<ST>(g.dst, g.plane, a, (int)cell,
-                   w * (P.f_forced ? ph * (1.0f + poly) : P.three_gamma_f * m + ph * poly), g.sf);
+        st_pop<ST>(g.dst, a, cell, w * (P.f_forced ? ph * (1.0f + poly) : P.three_gamma_f * m + ph * poly), g.sf);
       }
-      st_pop<ST>(g.dst, g.plane, Q + a, (int)cell, geq, g.sg);
+      st_pop<ST>(g.dst, Q + a, cell, geq, g.sg);
     }
   }
 }

@@ -267,16 +267,20 @@ def test_c1_static_droplet(lbm, rf):
 
 
 def test_c2_falling_droplet_until_divergence(lbm):
-    """c2 (256x1024, walls, rho 1:0.01): parity while finite; both sides diverge (the
-    central-difference scheme's density-ratio limit) at the same step."""
+    """c2 (256x1024, walls, rho 1:0.01): 1e-5 at steps 30 and 100 (measured 1.5e-6 and
+    3.6e-6; the gap grows only as the run nears its divergence, after step 125); both sides
+    diverge (the central-difference scheme's density-ratio limit) at the same step."""
     w = W.falling_droplet()
     sim = lbm.Sim.from_workload(w)
     ref = oracle.Sim.from_workload(w)
     sim.step(30)
     ref.step(30)
-    assert_parity(sim.moments(), ref.moments(), w, tol=1e-4)
+    assert_parity(sim.moments(), ref.moments(), w)
+    sim.step(70)
+    ref.step(70)
+    assert_parity(sim.moments(), ref.moments(), w)
     first = {}
-    for k in range(30, 600):
+    for k in range(100, 600):
         for name, s in (("gpu", sim), ("ref", ref)):
             if name not in first and not s.diagnostics()["finite"]:
                 first[name] = k
@@ -290,17 +294,21 @@ def test_c2_falling_droplet_until_divergence(lbm):
 
 @pytest.mark.parametrize("tile", [None, (128, 15), (128, 20), (256, 16)])
 def test_c3_splash_until_divergence(lbm, tile):
-    """c3 (2048x512, rho 1:0.001, Re 500, We 8000): parity over the first steps at full size,
-    with the default tile (one wave of CTAs) and with the tiles the benchmark's tuner chooses
-    between on GB300 (128 threads x 15 rows: 595 CTAs, 4 per SM; 128 x 20: 3 per SM; 256 x 16);
-    both sides diverge within the first dozen steps."""
+    """c3 (2048x512, rho 1:0.001, Re 500, We 8000): 1e-5 after 3 and 5 steps at full size
+    (measured 1.5e-6 and 1.6e-6; from step 6 the run's own instability amplifies rounding), with
+    the default tile (one wave of CTAs) and with the tiles the benchmark's tuner chooses between
+    on GB300 (128 threads x 15 rows: 595 CTAs, 4 per SM; 128 x 20: 3 per SM; 256 x 16); both
+    sides diverge within the first dozen steps."""
     w = W.splash()
     sim = lbm.Sim.from_workload(w, tile=tile)
     ref = oracle.Sim.from_workload(w)
     sim.step(3)
     ref.step(3)
-    assert_parity(sim.moments(), ref.moments(), w, tol=1e-4)
-    for _ in range(20):
+    assert_parity(sim.moments(), ref.moments(), w)
+    sim.step(2)
+    ref.step(2)
+    assert_parity(sim.moments(), ref.moments(), w)
+    for _ in range(18):
         sim.step(1)
         ref.step(1)
     assert not sim.diagnostics()["finite"] and not ref.diagnostics()["finite"]
