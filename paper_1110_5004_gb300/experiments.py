@@ -28,6 +28,66 @@ import numpy as np
 from . import Sim
 
 KEYS = ("spread_radius", "centroid_x", "centroid_y", "vel_y", "liquid_area", "sum_phi", "finite")
+CONTOUR_LEVEL = 0.55          # the paper's density contours (rho = 0.55, between rho_G = 0.1 and rho_L = 1)
+
+
+def contour_segments(field, level=CONTOUR_LEVEL):
+    """Iso-line field == level by marching squares on the cell-centre grid: an (n, 2, 2) array
+    of segments [[x0, y0], [x1, y1]] in lattice units (x along columns, y along rows), each
+    endpoint linearly interpolated on a square's edge.  Saddle squares join the corners by the
+    sign of the square's mean."""
+    f = np.asarray(field, dtype=np.float64) - level
+    a, b, c, d = f[:-1, :-1], f[:-1, 1:], f[1:, 1:], f[1:, :-1]   # corners (x,y), (x+1,y), (x+1,y+1), (x,y+1)
+    yy, xx = np.mgrid[0:f.shape[0] - 1, 0:f.shape[1] - 1].astype(np.float64)
+
+    def cut(v0, v1):
+        den = v0 - v1
+        return np.where(den != 0, v0 / np.where(den != 0, den, 1.0), 0.5)
+
+    # edge points: bottom (a-b), right (b-c), top (d-c), left (a-d)
+    pts = {"B": np.stack([xx + cut(a, b), yy], -1), "R": np.stack([xx + 1, yy + cut(b, c)], -1),
+           "T": np.stack([xx + cut(d, c), yy + 1], -1), "L": np.stack([xx, yy + cut(a, d)], -1)}
+    code = (a > 0).astype(int) | ((b > 0).astype(int) << 1) | ((c > 0).astype(int) << 2) | ((d > 0).astype(int) << 3)
+    mean_pos = (a + b + c + d) > 0
+    table = {1: [("L", "B")], 2: [("B", "R")], 3: [("L", "R")], 4: [("R", "T")], 6: [("B", "T")],
+             7: [("L", "T")], 8: [("T", "L")], 9: [("T", "B")], 11: [("T", "R")], 12: [("R", "L")],
+             13: [("R", "B")], 14: [("B", "L")]}
+    segs = []
+    for k, edges in table.items():
+        m = code == k
+        for e0, e1 in edges:
+            segs.append(np.stack([pts[e0][m], pts[e1][m]], 1))
+    for k, joined, split in ((5, [("L", "T"), ("B", "R")], [("L", "B"), ("R", "T")]),
+                             (10, [("B", "L"), ("T", "R")], [("B", "R"), ("T", "L")])):
+        for sel, edges in ((mean_pos, joined), (~mean_pos, split)):
+            m = (code == k) & sel
+            for e0, e1 in edges:
+                segs.append(np.stack([pts[e0][m], pts[e1][m]], 1))
+    return np.concatenate(segs, 0) if segs else np.zeros((0, 2, 2))
+
+
+def liquid_regions(rho, level=CONTOUR_LEVEL, periodic_x=True):
+    """Number of connected regions with rho >= level (8-neighbour connectivity, joined across a
+    periodic x boundary): the drop, the film and any secondary droplets."""
+    from scipy import ndimage
+    mask = np.asarray(rho) >= level
+    lab, n = ndimage.label(mask, structure=np.ones((3, 3), int))
+    if periodic_x and n > 1:
+        parent = list(range(n + 1))
+
+        def find(i):
+            while parent[i] != i:
+                parent[i] = parent[parent[i]]
+                i = parent[i]
+            return i
+        left, right = lab[:, 0], lab[:, -1]
+        for y in range(lab.shape[0]):
+            for dy in (-1, 0, 1):
+                yy = y + dy
+                if 0 <= yy < lab.shape[0] and left[y] and right[yy]:
+                    parent[find(left[y])] = find(right[yy])
+        n = len({find(i) for i in range(1, n + 1)})
+    return int(n)
 
 
 def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
@@ -56,7 +116,9 @@ def run_pair(make, steps, every, snapshot_steps=(), stream=None, variants=None):
             fa_y = sim.interfacial_force()["fay"]
             series["max_abs_fa_y"].append(float(np.abs(fa_y).max()) if d["finite"] else float("nan"))
             if done in snapshot_steps:
-                snaps[done] = {"rho": sim.moments()["rho"], "fa_y": fa_y}
+                rho = sim.moments()["rho"]
+                snaps[done] = {"rho": rho, "fa_y": fa_y, "contour": contour_segments(rho),
+                               "liquid_regions": liquid_regions(rho) if d["finite"] else None}
             if done >= steps or not d["finite"]:
                 break
             n = min(every, steps - done)
@@ -115,9 +177,17 @@ def falling_drop(steps=19000, every=100, snapshot_steps=(), stream=None, direct_
     return res
 
 
-def splash(Re, steps=3000, every=50, snapshot_steps=(), stream=None, f_form=0):
-    """f_form: the order-parameter LBE (0: equilibrium with the mu term, 1: forced form)."""
+SPLASH_T_STAR = (1.2, 1.8, 2.0)   # the paper's Fig. 2 / Fig. 3 times
+
+
+def splash(Re, steps=3000, every=50, snapshot_steps=None, stream=None, f_form=0):
+    """f_form: the order-parameter LBE (0: equilibrium with the mu term, 1: forced form).
+    Snapshots (density, its rho = 0.55 contour, the count of liquid regions, F_a,y) default to
+    the paper's t* = 1.2, 1.8 and 2.0 (t* = t U / D, U = 0.04, D = 60)."""
     import workloads as W
+    if snapshot_steps is None:
+        snapshot_steps = tuple(int(round(ts * 60.0 / 0.04)) for ts in SPLASH_T_STAR)
+    snapshot_steps = tuple(s for s in snapshot_steps if s % every == 0 and s <= steps)
     res = run_pair(lambda remove_Fa: _with_f_form(W.paper_splash(Re=Re, steps=steps, remove_Fa=remove_Fa), f_form),
                    steps, every, snapshot_steps, stream)
     t, dr = difference(res)
@@ -132,15 +202,23 @@ def splash(Re, steps=3000, every=50, snapshot_steps=(), stream=None, f_form=0):
                       "max_abs_fa_y_original": {"step": o["step"][idx[-1]], "value": o["max_abs_fa_y"][idx[-1]]}
                       if idx else None,
                       "max_abs_spread_radius_difference": float(np.max(np.abs(dr))),
-                      "spread_radius_difference_at_end": float(dr[-1])}
+                      "spread_radius_difference_at_end": float(dr[-1]),
+                      "liquid_regions": {k: {int(st): sn["liquid_regions"] for st, sn in res[k]["snapshots"].items()}
+                                         for k in ("original", "corrected")},
+                      "contour_segments": {k: {int(st): int(len(sn["contour"])) for st, sn in res[k]["snapshots"].items()}
+                                           for k in ("original", "corrected")}}
     return res
 
 
 def _jsonable(res):
+    """The results without field arrays; contours stay, as lists of segments."""
     out = {}
     for k, v in res.items():
         if isinstance(v, dict):
-            out[k] = {kk: vv for kk, vv in v.items() if kk != "snapshots"}
+            o = {kk: vv for kk, vv in v.items() if kk != "snapshots"}
+            if "snapshots" in v:
+                o["contours"] = {int(st): sn["contour"].round(3).tolist() for st, sn in v["snapshots"].items()}
+            out[k] = o
         else:
             out[k] = v
     return out
