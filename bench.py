@@ -53,6 +53,8 @@ def parse():
                     help="main-line workload: the 2048x512 splash, or the 4096x4096 periodic static drop")
     ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
                     help="population storage of the main line (16-bit forms keep FP32 arithmetic)")
+    ap.add_argument("--no-flush", action="store_true",
+                    help="no L2 flush between timed steps (for DRAM-traffic captures of consecutive steps)")
     ap.add_argument("--batch-sims", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--serve-requests", type=int, default=64)
@@ -437,7 +439,8 @@ def run_ours(args):
         for i in range(args.steps):
             if i % REINIT_EVERY == 0:
                 reinit()
-            flush_l2(i)
+            if not args.no_flush:
+                flush_l2(i)
             ev0[i].record(stream)
             sim.step(1)
             ev1[i].record(stream)
@@ -471,10 +474,33 @@ def run_ours(args):
         sim.step(REINIT_EVERY)
         sim.moments(h_out_np)
 
-    e2e_value = None
+    # the same work as two jobs in flight: two simulations on two streams, each driven by its own
+    # host thread through the packed calls (one upload and one download per iteration), so that
+    # one job's host copies overlap the other's steps
+    h_block = torch.from_numpy(np.stack([getattr(w, k) for k in ("phi0", "ux0", "uy0", "p0")])).pin_memory().numpy()
+    h_res = [torch.empty((5, w.ny, w.nx), dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
+    side = torch.cuda.Stream()
+    sims2 = [sim, lbm.Sim.from_workload(w, stream=side, tile=tile, storage=storage)]
+
+    def e2e_job(j, iters):
+        s = sims2[j]
+        for _ in range(iters):
+            s.init_fields_packed(h_block)
+            s.step(REINIT_EVERY)
+            s.moments_packed(h_res[j])
+
+    def e2e_pipelined(iters):
+        th = [threading.Thread(target=e2e_job, args=(j, n)) for j, n in enumerate((iters - iters // 2, iters // 2))]
+        for t_ in th:
+            t_.start()
+        for t_ in th:
+            t_.join()
+
+    e2e_value = e2e_serial = None
     if args.e2e_iters > 0:
         for _ in range(2):
             e2e_iter()
+        e2e_pipelined(4)
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -482,9 +508,17 @@ def run_ours(args):
         for _ in range(args.e2e_iters):
             e2e_iter()
         torch.cuda.synchronize()
+        e2e_serial, _ = replica_throughput(time.perf_counter() - t0, w.cells * REINIT_EVERY * args.e2e_iters,
+                                           world, device="cuda")
+        assert np.isfinite(h_out_np["phi"]).all(), "non-finite state inside the re-initialisation window"
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_pipelined(args.e2e_iters)
+        torch.cuda.synchronize()
         e2e_value, _ = replica_throughput(time.perf_counter() - t0, w.cells * REINIT_EVERY * args.e2e_iters,
                                           world, device="cuda")
-        assert np.isfinite(h_out_np["phi"]).all(), "non-finite state inside the re-initialisation window"
+        assert all(np.isfinite(r[0]).all() for r in h_res), "non-finite state inside the re-initialisation window"
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -515,9 +549,13 @@ def run_ours(args):
                 "e2e": {"value": e2e_value, "unit": "MLUPS",
                         "h2d_bytes_per_step": 4 * 4 * w.cells // REINIT_EVERY,
                         "d2h_bytes_per_step": 5 * 4 * w.cells // REINIT_EVERY,
-                        "what": "per iteration: lbm_init_fields from pinned host (4 fields), lbm_step(%d), "
-                                "lbm_moments to pinned host (5 fields); bytes shown per LBM step"
-                                % REINIT_EVERY},
+                        "what": "per iteration: lbm_init_fields_packed from a pinned host block (4 fields), "
+                                "lbm_step(%d), lbm_moments_packed into a pinned host block (5 fields); two "
+                                "simulations on two streams, each driven by its own host thread; bytes shown "
+                                "per LBM step" % REINIT_EVERY,
+                        "serial_value": e2e_serial,
+                        "serial_what": "one simulation, per-field lbm_init_fields / lbm_moments, iterations "
+                                       "back to back"},
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "cpu_baseline": cpu,

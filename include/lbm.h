@@ -159,6 +159,17 @@ LBM_API int lbm_step(lbm_sim* sim, int n);
  * simulation's work planes. */
 LBM_API int lbm_moments(lbm_sim* sim, float* phi, float* rho, float* ux, float* uy, float* p);
 
+/* The same two calls with every field in one caller-owned block, so that a transfer is one copy
+ * instead of one per field (no counterpart in the paper: a transfer-cost measure).
+ * lbm_init_fields_packed: `fields` holds phi0, ux0, uy0, p0 one after the other (4 nx*ny
+ *   float32, row-major; host or device); otherwise as lbm_init_fields (host memory is consumed
+ *   before return).
+ * lbm_moments_packed: writes phi, rho, ux, uy, p of the current state one after the other into
+ *   `fields` (5 nx*ny float32, host or device) and synchronises the stream.
+ * Errors: LBM_ERR_INVALID_ARG for NULL arguments, LBM_ERR_CUDA for launch or copy failures. */
+LBM_API int lbm_init_fields_packed(lbm_sim* sim, const float* fields);
+LBM_API int lbm_moments_packed(lbm_sim* sim, float* fields);
+
 /* The additional interfacial force of the current state (Eq. 12: F_a = -u [d_t rho + div(rho u)],
  * evaluated as -u s with u the state's velocity and s the mass defect by the simulation's s_form:
  * Eq. 5's rho' theta_M lap(mu), or the direct form from the stored density and flux), whether or

@@ -121,6 +121,19 @@ class Sim:
     def init_fields(self, phi0, ux0=None, uy0=None, p0=None):
         _lib.check(lib().lbm_init_fields(self._h, _ptr(phi0), _ptr(ux0), _ptr(uy0), _ptr(p0)))
 
+    def init_fields_packed(self, fields):
+        """lbm_init_fields_packed: phi0, ux0, uy0, p0 in one (4, ny, nx) float32 block (host
+        array or device tensor), copied in one transfer."""
+        _lib.check(lib().lbm_init_fields_packed(self._h, _ptr(fields)))
+
+    def moments_packed(self, out=None):
+        """lbm_moments_packed: phi, rho, ux, uy, p into one (5, ny, nx) float32 block (a new
+        host array, or the given host array / device tensor)."""
+        if out is None:
+            out = np.empty((5, self.ny, self.nx), np.float32)
+        _lib.check(lib().lbm_moments_packed(self._h, _ptr(out)))
+        return out
+
     def step(self, n=1):
         _lib.check(lib().lbm_step(self._h, int(n)))
 

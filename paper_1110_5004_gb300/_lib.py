@@ -24,7 +24,7 @@ EXPORTS = (
     "lbm_set_tile", "lbm_launch_count", "lbm_strerror", "lbm_last_error", "lbm_batch_create",
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
     "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
-    "lbm_checkpoint", "lbm_restore", "lbm_sim_device_bytes",
+    "lbm_checkpoint", "lbm_restore", "lbm_sim_device_bytes", "lbm_init_fields_packed", "lbm_moments_packed",
 )
 
 
@@ -70,6 +70,8 @@ def load(path: str = LIB_PATH):
         "lbm_init_fields": (ip, [vp, fp, fp, fp, fp]),
         "lbm_step": (ip, [vp, ip]),
         "lbm_moments": (ip, [vp, fp, fp, fp, fp, fp]),
+        "lbm_init_fields_packed": (ip, [vp, fp]),
+        "lbm_moments_packed": (ip, [vp, fp]),
         "lbm_interfacial_force": (ip, [vp, fp, fp]),
         "lbm_diagnostics": (ip, [vp, ctypes.POINTER(lbm_diag)]),
         "lbm_destroy": (ip, [vp]),

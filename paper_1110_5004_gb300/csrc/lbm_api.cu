@@ -264,6 +264,42 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
   return LBM_OK;
 }
 
+// nplanes consecutive nx*ny fields between consecutive pitched work planes (starting at plane
+// k0) and a caller's packed block: one copy (one 2D copy when the pitch differs from nx).
+static cudaError_t copy_planes(const lbm_sim* s, int k0, int nplanes, float* packed, bool to_work,
+                               cudaMemcpyKind kind) {
+  float* work = s->fields + (long long)k0 * s->plane;
+  const size_t row = (size_t)s->nx * sizeof(float), wpitch = (size_t)s->pitch * sizeof(float);
+  const size_t rows = (size_t)nplanes * s->ny;   // consecutive work planes are ny pitched rows apart
+  if (wpitch == row) {
+    return to_work ? cudaMemcpyAsync(work, packed, row * rows, kind, s->stream)
+                   : cudaMemcpyAsync(packed, work, row * rows, kind, s->stream);
+  }
+  return to_work ? cudaMemcpy2DAsync(work, wpitch, packed, row, row, rows, kind, s->stream)
+                 : cudaMemcpy2DAsync(packed, row, work, wpitch, row, rows, kind, s->stream);
+}
+
+int lbm_init_fields_packed(lbm_sim* s, const float* fields) {
+  Range range_("lbm_init_fields_packed");
+  if (!s || !fields) return set_error("sim and fields are required"), LBM_ERR_INVALID_ARG;
+  const bool host = !is_device_ptr(fields);
+  const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const size_t n = (size_t)s->nx * s->ny;
+  float* in = const_cast<float*>(fields);   // read only: copied into the work planes
+  // phi0 -> work plane 0; ux0, uy0, p0 -> work planes 2, 3, 4 (consecutive)
+  cudaError_t e = copy_planes(s, 0, 1, in, true, kind);
+  if (e == cudaSuccess) e = copy_planes(s, 2, 3, in + n, true, kind);
+  if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields_packed upload");
+  e = launch_init(s, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields_packed launch");
+  s->launches += s->params.s_form ? 3 : 2;
+  s->steps = 0;
+  if (host && (e = cudaEventSynchronize(s->uploaded)) != cudaSuccess)
+    return cuda_fail(e, "lbm_init_fields_packed sync");
+  return LBM_OK;
+}
+
 int lbm_step(lbm_sim* s, int n) {
   Range range_("lbm_step");
   if (!s || n < 0) return set_error("invalid sim or step count"), LBM_ERR_INVALID_ARG;
@@ -337,6 +373,28 @@ int lbm_moments(lbm_sim* s, float* phi, float* rho, float* ux, float* uy, float*
   if (e != cudaSuccess) return cuda_fail(e, "moments launch");
   s->launches++;
   return copy_out(s, staged, 5, "lbm_moments copy");
+}
+
+int lbm_moments_packed(lbm_sim* s, float* fields) {
+  Range range_("lbm_moments_packed");
+  if (!s || !fields) return set_error("sim and fields are required"), LBM_ERR_INVALID_ARG;
+  const size_t n = (size_t)s->nx * s->ny;
+  // a device block with rows of the work pitch is written by the moment pass itself
+  float* direct = direct_target(s, fields);
+  float* dst = direct ? direct : s->fields;
+  const size_t stride = direct ? n : (size_t)s->plane;
+  Grid g = make_grid(s, s->buf[s->cur], nullptr);
+  MomentOut mo{dst, dst + stride, dst + 2 * stride, dst + 3 * stride, dst + 4 * stride};
+  cudaError_t e = launch_moments(s->phys, g, mo, s->nt, s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_moments_packed launch");
+  s->launches++;
+  if (!direct) {
+    const cudaMemcpyKind kind = is_device_ptr(fields) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    e = copy_planes(s, 0, 5, fields, false, kind);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_moments_packed copy");
+  }
+  e = cudaStreamSynchronize(s->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(e, "lbm_moments_packed sync");
 }
 
 int lbm_interfacial_force(lbm_sim* s, float* fa_x, float* fa_y) {

@@ -108,13 +108,26 @@ static int rebuild(lbm_batch* b) {
   // interleave the members' tiles so concurrent CTAs spread over simulations; the tiles of
   // members with the direct mass defect follow those of the others (a launch of their own)
   std::vector<std::vector<int4>> per[2];
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  set_batch_attr(b->nt, false);   // the occupancy query needs the shared-memory size admitted
+  const int slots = sms * std::max(batch_occupancy_sd<false>(b->nt), 1);
   for (size_t m = 0; m < members.size(); ++m) {
     lbm_sim* s = b->slots[members[m]];
     SimDesc d{};
     d.P = s->phys;
     Grid g = make_grid(s, nullptr, nullptr);
-    // one wave of the batch kernel is shared by all members: size segments for the batch
-    tile_geometry(s->nx, s->ny, b->nt, s->seg_h ? s->seg_h : b->seg_h, 0, &g.tile_w, &g.n_strips, &g.seg_h);
+    // one wave of the batch kernel is shared by all members: size segments for the batch.  A
+    // member large enough to fill the wave on its own gets segments of the height that does so
+    // (as a simulation stepped alone): fewer, taller tiles cut its pipeline-fill rows.
+    int h = s->seg_h ? s->seg_h : b->seg_h;
+    if (!s->seg_h) {
+      int tw = 0, ns = 0, hw = 0;
+      tile_geometry(s->nx, s->ny, b->nt, 0, slots, &tw, &ns, &hw);
+      h = std::max(h, hw);
+    }
+    tile_geometry(s->nx, s->ny, b->nt, h, 0, &g.tile_w, &g.n_strips, &g.seg_h);
     d.g = g;
     d.buf0 = s->buf[0];
     d.buf1 = s->buf[1];
@@ -162,9 +175,6 @@ static int rebuild(lbm_batch* b) {
   if ((e = cudaStreamSynchronize(b->stream)) != cudaSuccess) return cuda_fail(e, "batch upload sync");
   b->n_work = (int)work.size();
   b->n_plain = n_plain;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   b->grid_plain = b->grid_sd = 0;
   if (b->n_plain > 0) {
     if ((e = set_batch_attr(b->nt, false)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");

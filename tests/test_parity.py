@@ -437,6 +437,31 @@ def test_moments_into_pinned_host_and_device_buffers(lbm, nx):
         assert np.array_equal(got, ref[k]), ("mixed", k)
 
 
+@pytest.mark.parametrize("nx", [64, 45])
+def test_packed_fields_in_and_out(lbm, nx):
+    """lbm_init_fields_packed / lbm_moments_packed move every field in one block and one copy;
+    host and device blocks, rows equal to the work pitch (64) or not (45), give the state and the
+    moments of the per-field calls bitwise."""
+    import torch
+    w = W.random_small(nx, 27, seed=15, bc_y=W.WALL, gravity=1e-5, remove_Fa=1)
+    ref = lbm.Sim.from_workload(w)
+    ref.step(9)
+    want = ref.moments()
+    block = np.stack([w.phi0, w.ux0, w.uy0, w.p0]).astype(np.float32)
+    names = ("phi", "rho", "ux", "uy", "p")
+    for where in ("host", "device"):
+        s = lbm.Sim(w.nx, w.ny, lbm.params_from_physical(w.phys))
+        src = block if where == "host" else torch.from_numpy(block).cuda()
+        s.init_fields_packed(src)
+        s.step(9)
+        assert np.array_equal(s.checkpoint(), ref.checkpoint()), where
+        out = None if where == "host" else torch.full((5, w.ny, w.nx), float("nan"), device="cuda")
+        got = s.moments_packed(out)
+        got = got if where == "host" else got.cpu().numpy()
+        for k, name in enumerate(names):
+            assert np.array_equal(got[k], want[name]), (where, name)
+
+
 def test_zero_steps_and_null_outputs(lbm):
     w = W.random_small(16, 16, seed=1)
     s = lbm.Sim.from_workload(w)
