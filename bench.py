@@ -57,7 +57,7 @@ def parse():
                     help="no L2 flush between timed steps (for DRAM-traffic captures of consecutive steps)")
     ap.add_argument("--batch-sims", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=2000)
-    ap.add_argument("--serve-requests", type=int, default=64)
+    ap.add_argument("--serve-requests", type=int, default=256)
     ap.add_argument("--serve-step-scale", type=float, default=0.2)
     return ap.parse_args()
 
@@ -227,7 +227,7 @@ def batch_leg(args, lbm, torch):
     stream = torch.cuda.current_stream()
     out = {"sims": len(ws), "steps": args.batch_steps, "cells": cells,
            "workload": "c4 ragged batch, seed 1234"}
-    for st, name in ((0, "fp32"), (2, "bf16")):
+    for st, name in ((0, "fp32"), (1, "fp16"), (2, "bf16")):
         sims = [lbm.Sim.from_workload(w, storage=st, stream=stream) for w in ws]
         b = lbm.Batch(stream=stream)
         for s in sims:
@@ -238,13 +238,21 @@ def batch_leg(args, lbm, torch):
         b.step(args.batch_steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        finite = sum(s.diagnostics()["finite"] for s in sims)
+        ok = [s.diagnostics()["finite"] for s in sims]
+        cells_ok = sum(w.cells for w, f in zip(ws, ok) if f)
         out[name] = {"aggregate_mlups": cells * args.batch_steps / dt / 1e6, "seconds": dt,
-                     "tile": list(tile[:2]), "finite_at_end": finite}
+                     "tile": list(tile[:2]), "finite_at_end": int(sum(ok)),
+                     "mlups_finite": cells_ok * args.batch_steps / dt / 1e6}
         b.close()
         for s in sims:
             s.close()
     out["back_to_back_fp32_mlups"] = None
+    out["accuracy"] = {"fp32": "FP32 parity with the FP64 oracle (1e-5)",
+                       "fp16": "within the reduced-storage bound (phi 1e-3; drift and centroid velocity 0.5 %)",
+                       "bf16": "misses the reduced-storage bound (falling drop: 3.8 % in centroid velocity, "
+                               "1.6 % in phi): not a same-accuracy figure"}
+    out["finite_note"] = ("members at density ratios 100 and 1000 leave the finite range under this "
+                          "scheme; mlups_finite counts only the members finite after the run")
     return out
 
 
@@ -349,6 +357,8 @@ def storage16_leg(lbm, torch, w, peak, flush_l2, steps=48):
         sim.close()
     out["workload"] = w.name
     out["l2"] = "flushed between timed steps, as the main line"
+    out["accuracy"] = {"fp16": "within the reduced-storage bound (phi 1e-3 of the FP64 oracle)",
+                       "bf16": "misses the reduced-storage bound on a falling drop: not a same-accuracy figure"}
     return out
 
 

@@ -139,7 +139,10 @@ LBM_API size_t lbm_sim_device_bytes(const lbm_sim* sim);
 /* Create a simulation on the current CUDA device.  nx, ny >= 3 (>= 4 along a walled axis),
  * and ny * pitch * 76 B < 2 GiB (pitch = nx rounded up to 32: about 28 M cells); parameters
  * are validated (tau > 1/2, densities, beta, kappa, phi* > 0, theta_M >= 0).
- * cuda_stream: a cudaStream_t (may be NULL).  On success *out owns cudaMalloc'd state.
+ * cuda_stream: a cudaStream_t (may be NULL).  On success *out owns its device state: stream-ordered
+ * allocations from the device's default memory pool on cuda_stream (no device-wide
+ * synchronisation, so a simulation can be created while others run), returned to the pool by
+ * lbm_destroy.
  * Errors: LBM_ERR_INVALID_ARG, LBM_ERR_OOM (device allocation failed), LBM_ERR_CUDA. */
 LBM_API int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_sim** out);
 
@@ -209,7 +212,8 @@ LBM_API size_t lbm_checkpoint_bytes(const lbm_sim* sim);
 LBM_API int lbm_checkpoint(lbm_sim* sim, void* buf, size_t bytes);
 LBM_API int lbm_restore(lbm_sim* sim, const void* buf, size_t bytes);
 
-/* Replace the stream the simulation queues its work on (cudaStream_t, may be NULL). */
+/* Replace the stream the simulation queues its work on (cudaStream_t, may be NULL).  The previous
+ * stream is synchronised first (the state's allocation and earlier work are ordered on it). */
 LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
 
 /* Tile shape of the fused step kernel: threads per CTA (64, 128 or 256; the CTA covers
@@ -258,8 +262,9 @@ LBM_API int lbm_diagnostics_fields_noalloc(const float* phi, const float* ux, co
  * A batch advances many independent simulations (different sizes and parameters) with one
  * launch per time step over a work list of tiles from all of them.  Simulations stay owned by
  * the caller; the batch references them.  budget_bytes caps the summed lbm_device_bytes of
- * its members (0 = no cap).  lbm_batch_step(k) advances every member by k steps (one CUDA
- * graph replay for a fixed membership); members keep stepping on the batch's stream. */
+ * its members (0 = no cap).  lbm_batch_step(k) advances every member by k steps (replays of one
+ * 16-step CUDA graph captured per membership, the rest launched directly); members keep stepping
+ * on the batch's stream. */
 typedef struct lbm_batch lbm_batch;
 
 LBM_API int lbm_batch_create(size_t budget_bytes, void* cuda_stream, lbm_batch** out);

@@ -196,11 +196,16 @@ int lbm_create(int nx, int ny, const lbm_params* params, void* cuda_stream, lbm_
     return rc;
   }
   s->occ = tile_occupancy(s->nt);
-  if ((e = cudaMalloc(&s->buf[0], s->buf_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&s->buf[1], s->buf_bytes)) != cudaSuccess ||
-      (e = cudaMalloc(&s->fields, (size_t)N_FIELDS * s->plane * sizeof(float))) != cudaSuccess ||
-      (e = cudaMalloc(&s->red, ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double))) != cudaSuccess ||
-      (e = cudaMallocHost(&s->h_diag, sizeof(lbm_diag))) != cudaSuccess ||
+  // Stream-ordered allocations from the device's memory pool, on the simulation's stream: unlike
+  // cudaMalloc they do not order the other streams of the device, so a server can create a
+  // simulation while others run.  The memory is ordered on s->stream (lbm_set_stream and
+  // lbm_batch_add synchronise it before other streams use the state).
+  if ((e = cudaMallocAsync(&s->buf[0], s->buf_bytes, s->stream)) != cudaSuccess ||
+      (e = cudaMallocAsync(&s->buf[1], s->buf_bytes, s->stream)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->fields), (size_t)N_FIELDS * s->plane * sizeof(float),
+                           s->stream)) != cudaSuccess ||
+      (e = cudaMallocAsync(reinterpret_cast<void**>(&s->red), ((size_t)ny * DIAG_PARTIALS + 16) * sizeof(double),
+                           s->stream)) != cudaSuccess ||
       (e = cudaEventCreateWithFlags(&s->uploaded, cudaEventDisableTiming)) != cudaSuccess) {
     rc = cuda_fail(e, "lbm_create allocation");
     lbm_destroy(s);
@@ -419,11 +424,11 @@ int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {
   cudaError_t e = launch_diag(s, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics launch");
   s->launches += 2;
-  e = cudaMemcpyAsync(s->h_diag, s->red + (long long)s->ny * DIAG_PARTIALS, sizeof(lbm_diag),
+  e = cudaMemcpyAsync(&s->h_diag, s->red + (long long)s->ny * DIAG_PARTIALS, sizeof(lbm_diag),
                       cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
-  *out = *s->h_diag;
+  *out = s->h_diag;
   if (!out->finite) {
     set_error("simulation diverged (non-finite state) at step %lld", out->step);
     return LBM_ERR_DIVERGED;
@@ -434,11 +439,9 @@ int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {
 int lbm_destroy(lbm_sim* s) {
   if (!s) return LBM_OK;
   if (s->stream || s->buf[0]) cudaStreamSynchronize(s->stream);
-  cudaFree(s->buf[0]);
-  cudaFree(s->buf[1]);
-  cudaFree(s->fields);
-  cudaFree(s->red);
-  if (s->h_diag) cudaFreeHost(s->h_diag);
+  // back to the pool, ordered on the stream: no device-wide synchronisation
+  for (void* p : {s->buf[0], s->buf[1], static_cast<void*>(s->fields), static_cast<void*>(s->red)})
+    if (p) cudaFreeAsync(p, s->stream);
   if (s->uploaded) cudaEventDestroy(s->uploaded);
   delete s;
   return LBM_OK;
@@ -519,6 +522,9 @@ int lbm_restore(lbm_sim* s, const void* buf, size_t bytes) {
 
 int lbm_set_stream(lbm_sim* s, void* stream) {
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  // the state's allocation and earlier work are ordered on the old stream
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "lbm_set_stream sync");
   s->stream = (cudaStream_t)stream;
   return LBM_OK;
 }

@@ -1,8 +1,8 @@
 // Ragged batches: many independent simulations (any sizes and parameters) advanced by one
 // persistent launch per time step over a work list of (simulation, strip, segment) tiles; two
 // launches when some members use the direct mass defect (its tiles run in their own kernel
-// instance).  k steps are captured once as a CUDA graph and replayed while the membership is
-// unchanged.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel
+// instance).  Steps run as replays of one 16-step CUDA graph captured once per membership, the
+// remainder of a step count as direct launches.  Each tile runs exactly the per-cell arithmetic of the single-simulation kernel
 // (every operation an explicit round-to-nearest intrinsic), so a member's state is bitwise the
 // same alone or inside any mix.
 #include <algorithm>
@@ -75,6 +75,8 @@ static int batch_occupancy_sd(int nt) {
   return occ;
 }
 
+constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even: parity-neutral)
+
 struct lbm_batch {
   size_t budget = 0;
   size_t bytes = 0;
@@ -91,7 +93,7 @@ struct lbm_batch {
   int n_plain = 0;                     // work[0, n_plain): members without the direct mass defect
   int grid_plain = 0, grid_sd = 0;     // persistent grid of each launch
   int flip = 0;                        // parity offset of every member since the last rebuild
-  std::map<int, cudaGraphExec_t> graphs;  // 2k + flip -> executable graph for the membership
+  std::map<int, cudaGraphExec_t> graphs;  // flip -> executable graph of GRAPH_STEPS steps
 };
 
 static void drop_graphs(lbm_batch* b) {
@@ -277,26 +279,35 @@ int lbm_batch_step(lbm_batch* b, int k) {
   int rc;
   if (b->dirty && (rc = rebuild(b))) return rc;
   if (b->n_work == 0) return LBM_OK;
-  cudaGraphExec_t exec = nullptr;
-  const int key = 2 * k + b->flip;
-  auto it = b->graphs.find(key);
-  if (it != b->graphs.end()) {
-    exec = it->second;
-  } else {
-    cudaGraph_t graph;
-    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
-    for (int i = 0; i < k && e == cudaSuccess; ++i) e = launch_batch(b, b->flip + i, b->cap);
-    cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
-    if (e != cudaSuccess) return cuda_fail(e, "batch capture launch");
-    if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture end");
-    e = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
-    b->graphs[key] = exec;
+  // Whole blocks of GRAPH_STEPS steps replay one graph captured once per membership (the block
+  // is even, so a replay leaves the buffer parity as it found it); the remaining k mod
+  // GRAPH_STEPS steps are launched directly.  Round lengths then vary freely without a new
+  // capture each time.
+  const int blocks = k / GRAPH_STEPS, rest = k % GRAPH_STEPS;
+  cudaError_t e = cudaSuccess;
+  if (blocks > 0) {
+    cudaGraphExec_t exec = nullptr;
+    auto it = b->graphs.find(b->flip);
+    if (it != b->graphs.end()) {
+      exec = it->second;
+    } else {
+      cudaGraph_t graph;
+      e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(e, "batch capture begin");
+      for (int i = 0; i < GRAPH_STEPS && e == cudaSuccess; ++i) e = launch_batch(b, b->flip + i, b->cap);
+      cudaError_t e2 = cudaStreamEndCapture(b->cap, &graph);
+      if (e != cudaSuccess) return cuda_fail(e, "batch capture launch");
+      if (e2 != cudaSuccess) return cuda_fail(e2, "batch capture end");
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "batch graph instantiate");
+      b->graphs[b->flip] = exec;
+    }
+    for (int i = 0; i < blocks && e == cudaSuccess; ++i) e = cudaGraphLaunch(exec, b->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
   }
-  cudaError_t e = cudaGraphLaunch(exec, b->stream);
-  if (e != cudaSuccess) return cuda_fail(e, "batch graph launch");
+  for (int i = 0; i < rest && e == cudaSuccess; ++i) e = launch_batch(b, b->flip + i, b->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "batch step launch");
   bool flip = (k & 1) != 0;
   for (lbm_sim* s : b->slots) {
     if (!s) continue;

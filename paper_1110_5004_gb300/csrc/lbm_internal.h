@@ -21,7 +21,8 @@ struct lbm_sim {
   int cur = 0;                         // buffer holding the current state
   float* fields = nullptr;             // 6 planes: phi, rho, ux, uy, p, mu (moments and init)
   double* red = nullptr;               // reduction scratch: ny rows x 12 partials + final record
-  lbm_diag* h_diag = nullptr;          // pinned host copy of the final record
+  lbm_diag h_diag{};                   // host copy of the final record (pageable: allocating
+                                       // page-locked memory would order the streams of the device)
   cudaEvent_t uploaded = nullptr;      // recorded after lbm_init_fields' host-to-device copies
   long long steps = 0;
   long long launches = 0;

@@ -32,6 +32,12 @@ class FakeSim:
     def moments(self):
         return {"phi": np.full((self.w.ny, self.w.nx), float(self.steps), np.float32)}
 
+    def set_stream(self, stream):
+        pass
+
+    def step(self, k):
+        self.steps += k
+
     def close(self):
         FakeSim.live -= 1
 
@@ -114,6 +120,25 @@ def test_admission_respects_budget_and_order(fake_server):
     assert FakeSim.live == 0                       # every member's memory was released
 
 
+def test_large_members_step_alone_within_the_budget(fake_server):
+    """Members of at least solo_cells cells step alone (their own kernel, not the batch), count
+    against the same budget, and finish, diverge and release memory like batch members."""
+    serve = fake_server
+    reqs = [_req(serve, 0, 20, 20, 200, 0.0),                  # 400 cells: alone
+            _req(serve, 1, 10, 10, 150, 0.0),                  # 100 cells: batched
+            _req(serve, 2, 20, 20, 300, 0.0, diverge_at=120),  # alone, goes non-finite
+            _req(serve, 3, 10, 10, 250, 0.0)]
+    srv = serve.Server(budget_bytes=1000, chunk_steps=60, check_steps=60, stream=0, solo_cells=400)
+    res = {r.rid: r for r in srv.run(reqs, realtime=False)}
+    assert res[0].status == "done" and res[0].steps_done == 200
+    assert res[1].status == "done" and res[1].steps_done == 150
+    assert res[2].status == "diverged" and res[2].steps_done == 120
+    assert res[3].status == "done" and res[3].steps_done == 250
+    assert max(n for _, n in srv.batch.history) <= 2          # only the small members batched
+    assert srv.max_bytes <= 1000 and srv.solo_bytes == 0 and srv.batch.bytes == 0
+    assert FakeSim.live == 0
+
+
 def test_rejection_divergence_and_cancellation(fake_server):
     serve = fake_server
     reqs = [_req(serve, 0, 10, 10, 300, 0.0),
@@ -194,10 +219,13 @@ def gpu_stream():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_alone(lbm):
+@pytest.mark.parametrize("solo_cells", [1 << 20, 4000])
+def test_served_results_equal_alone(lbm, solo_cells):
+    """Bitwise the results of the same requests run one by one; with solo_cells = 4000 the larger
+    requests step alone on the server stream next to the batch of the smaller ones."""
     from paper_1110_5004_gb300 import serve
     reqs = gpu_stream()
-    srv = serve.Server(budget_bytes=1 << 34, chunk_steps=64, keep_fields=True)
+    srv = serve.Server(budget_bytes=1 << 34, chunk_steps=64, keep_fields=True, solo_cells=solo_cells)
     served = srv.run(reqs)
     alone = serve.run_plain(reqs, keep_fields=True)
     assert srv.max_concurrent >= 2                      # work of several requests overlapped
