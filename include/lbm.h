@@ -51,6 +51,12 @@ extern "C" {
 #define LBM_FP16_DEV 1 /* 2-byte fp16 deviations from the lattice-weight baseline, FP32 math */
 #define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math */
 
+/* step kernel (lbm_set_kernel) */
+#define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel on grids of at most 524288 cells where it applies,
+                              else the row march */
+#define LBM_KERNEL_ROWS 1  /* strips marching rows: every configuration */
+#define LBM_KERNEL_TILES 2 /* 2-D tiles in four shared-memory passes: s_form 0, f_form 0 */
+
 /* return codes */
 #define LBM_OK 0
 #define LBM_ERR_INVALID_ARG (-1)
@@ -221,6 +227,14 @@ LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
  * simulation has 128 threads and as many rows per CTA as make one wave of resident CTAs
  * (at least 8 rows). */
 LBM_API int lbm_set_tile(lbm_sim* sim, int threads, int seg_rows);
+
+/* Step kernel of the simulation (no counterpart in the paper; both kernels compute every cell
+ * bitwise alike): LBM_KERNEL_AUTO (default), LBM_KERNEL_ROWS or LBM_KERNEL_TILES.  The row march
+ * streams large grids at the memory system's pace; on small grids its per-segment pipeline is
+ * latency-bound, and the tile kernel (one load round and four short passes per step) is faster.
+ * LBM_KERNEL_TILES needs s_form 0 and f_form 0 (else LBM_ERR_INVALID_ARG).  Takes effect at the
+ * next lbm_step; batches always run their own kernel. */
+LBM_API int lbm_set_kernel(lbm_sim* sim, int kernel);
 
 /* Kernel launches issued by this simulation since creation (step, init, moments,
  * reductions). */

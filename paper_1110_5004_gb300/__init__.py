@@ -12,11 +12,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (LBM_BF16_DEV, LBM_ERR_BUDGET, LBM_ERR_DIVERGED, LBM_FP16_DEV, LBM_FP32,
-                   LBM_PERIODIC, LBM_WALL, LBMError, lbm_diag, lbm_params)
+                   LBM_KERNEL_AUTO, LBM_KERNEL_ROWS, LBM_KERNEL_TILES, LBM_PERIODIC, LBM_WALL,
+                   LBMError, lbm_diag, lbm_params)
 
 __all__ = ["Sim", "Batch", "LBMError", "params_from_physical", "lbm_params", "LBM_FP32",
            "LBM_FP16_DEV", "LBM_BF16_DEV", "LBM_PERIODIC", "LBM_WALL", "LBM_ERR_DIVERGED",
-           "LBM_ERR_BUDGET", "device_bytes"]
+           "LBM_ERR_BUDGET", "LBM_KERNEL_AUTO", "LBM_KERNEL_ROWS", "LBM_KERNEL_TILES", "device_bytes"]
 
 
 def lib():
@@ -86,10 +87,14 @@ class Sim:
         self._h = h
 
     @classmethod
-    def from_workload(cls, w, storage=LBM_FP32, stream=None, init=True, tile=None):
+    def from_workload(cls, w, storage=LBM_FP32, stream=None, init=True, tile=None, kernel=None):
+        """A simulation of workload `w`.  `tile` (threads, rows) shapes the row march and selects it
+        unless `kernel` says otherwise; `kernel` is one of the LBM_KERNEL_* values."""
         s = cls(w.nx, w.ny, params_from_physical(w.phys, storage), stream=stream)
         if tile is not None:
             s.set_tile(*tile)
+        if kernel is not None or tile is not None:
+            s.set_kernel(LBM_KERNEL_ROWS if kernel is None else kernel)
         if init:
             s.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
         return s
@@ -114,6 +119,11 @@ class Sim:
         the current value of either (a simulation starts with as many rows per CTA as fill one
         wave of resident CTAs)."""
         _lib.check(lib().lbm_set_tile(self._h, int(threads), int(seg_rows)))
+
+    def set_kernel(self, kernel):
+        """Step kernel: LBM_KERNEL_AUTO, LBM_KERNEL_ROWS or LBM_KERNEL_TILES (bitwise the same
+        results; the tile kernel needs s_form 0 and f_form 0)."""
+        _lib.check(lib().lbm_set_kernel(self._h, int(kernel)))
 
     def set_stream(self, stream):
         _lib.check(lib().lbm_set_stream(self._h, _stream_handle(stream)))

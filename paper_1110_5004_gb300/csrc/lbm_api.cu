@@ -99,6 +99,11 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
   return g;
 }
 
+bool uses_tile2d(const lbm_sim* s) {
+  if (s->kernel == LBM_KERNEL_ROWS || !tile2d_eligible(s->params)) return false;
+  return s->kernel == LBM_KERNEL_TILES || (long long)s->nx * s->ny <= SMALL_GRID_CELLS;
+}
+
 static int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
 
 static bool is_device_ptr(const void* p) {
@@ -309,9 +314,10 @@ int lbm_step(lbm_sim* s, int n) {
   Range range_("lbm_step");
   if (!s || n < 0) return set_error("invalid sim or step count"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation is a batch member; step it through its batch"), LBM_ERR_INVALID_ARG;
+  const bool tiles = uses_tile2d(s);
   for (int i = 0; i < n; ++i) {
     Grid g = make_grid(s, s->buf[s->cur], s->buf[s->cur ^ 1]);
-    cudaError_t e = launch_step(s->phys, g, s->nt, s->stream);
+    cudaError_t e = tiles ? launch_tile2d(s->phys, g, s->stream) : launch_step(s->phys, g, s->nt, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_step launch");
     s->cur ^= 1;
     s->steps++;
@@ -539,6 +545,16 @@ int lbm_set_tile(lbm_sim* s, int threads, int seg_rows) {
     s->occ = tile_occupancy(threads);
   }
   if (seg_rows) s->seg_h = seg_rows;
+  return LBM_OK;
+}
+
+int lbm_set_kernel(lbm_sim* s, int kernel) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_ROWS && kernel != LBM_KERNEL_TILES)
+    return set_error("kernel must be LBM_KERNEL_AUTO, LBM_KERNEL_ROWS or LBM_KERNEL_TILES"), LBM_ERR_INVALID_ARG;
+  if (kernel == LBM_KERNEL_TILES && !tile2d_eligible(s->params))
+    return set_error("the tile kernel needs s_form 0 and f_form 0"), LBM_ERR_INVALID_ARG;
+  s->kernel = kernel;
   return LBM_OK;
 }
 

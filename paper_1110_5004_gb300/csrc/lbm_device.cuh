@@ -462,6 +462,101 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   }
 }
 
+// ---- Per-cell stage arithmetic, shared by every step kernel (the row march below and the 2-D
+// tile kernel), so that a cell's result does not depend on the kernel that computes it.  Stencil
+// arguments point at the cell's column in rows s (south), 0 and n (north); [-1] and [1] are the
+// west and east neighbours.
+
+// S0: phi = sum_a f_a as an unevaluated pair hi + lo (fp[0..8] f_0..f_8, fp[9] f_0lo).
+__device__ __forceinline__ void phi_pair(const float fp[NF], float& hi, float& lo) {
+  const float small =
+      fadd(fp[Q], fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8]))));
+  two_sum(fp[0], small, hi, lo);
+}
+
+// S1: mu = theta'(phi) - kappa lap(phi) (Eq. 1) from the phi pair's 3x3 neighbourhood.
+__device__ __forceinline__ float chem_potential(const Phys& P, const float* hs, const float* h0, const float* hn,
+                                               const float* ls, const float* l0, const float* ln) {
+  const float H = h0[0], L = l0[0];
+  // differences from the centre: exact for neighbouring values of like magnitude; the low
+  // words are tiny and are summed directly
+  const float dax = fadd(fadd(fsub(h0[1], H), fsub(hn[0], H)), fadd(fsub(h0[-1], H), fsub(hs[0], H)));
+  const float ddg = fadd(fadd(fsub(hn[1], H), fsub(hn[-1], H)), fadd(fsub(hs[-1], H), fsub(hs[1], H)));
+  const float lax = fadd(fadd(l0[1], ln[0]), fadd(l0[-1], ls[0]));
+  const float ldg = fadd(fadd(ln[1], ln[-1]), fadd(ls[-1], ls[1]));
+  const float lap6 = fmad(-20.0f, L, fmad(4.0f, fadd(dax, lax), fadd(ddg, ldg)));   // 6 lap(phi)
+  const float ph = fadd(H, L);
+  const float dm = fadd(fsub(H, P.phi_star), L), dp = fadd(fadd(H, P.phi_star), L);
+  return fmad(-P.kappa6, lap6, fmul(fmul(fmul(P.four_beta, ph), dm), dp));
+}
+
+// 6 lap(q) of the isotropic 9-point Laplacian.
+__device__ __forceinline__ float lap6_of(const float* s, const float* c, const float* n) {
+  return fmad(-20.0f, c[0], fmad(4.0f, fadd(fadd(c[1], n[0]), fadd(c[-1], s[0])), fadd(fadd(n[1], n[-1]), fadd(s[-1], s[1]))));
+}
+
+// S2: density, surface and body forces, velocity (the second-order scheme of Eq. 8, F_a removed
+// or not) and pressure of a cell from phi, 12 grad(phi), 12 grad(mu), mu, the mass defect s and
+// the pulled gbar populations.
+struct S2Out {
+  float rho, cl, fsx, fsy, gy, rrho, ux, uy, rx, ry, p;
+};
+__device__ __forceinline__ S2Out s2_cell(const Phys& P, float ph, float gphx, float gphy, float gmx, float gmy,
+                                         float mu0, float sdef, const float gb[Q]) {
+  S2Out o;
+  o.cl = __saturatef(fmad(ph, P.inv_2phistar, 0.5f));   // clamp((phi + phi*) / (2 phi*))
+  o.rho = fmad(o.cl, P.drho, P.rho_B);
+  if (P.fs_mu) {                                        // F_s = mu grad phi, or -phi grad mu
+    const float mu12 = fmul(mu0, 1.0f / 12.0f);
+    o.fsx = fmul(mu12, gphx);
+    o.fsy = fmul(mu12, gphy);
+  } else {
+    const float mph12 = fmul(ph, -1.0f / 12.0f);
+    o.fsx = fmul(mph12, gmx);
+    o.fsy = fmul(mph12, gmy);
+  }
+  o.gy = fmul(-P.gravity, o.rho);
+  const float s13 = fadd(gb[1], gb[3]), d13 = fsub(gb[1], gb[3]);
+  const float s24 = fadd(gb[2], gb[4]), d24 = fsub(gb[2], gb[4]);
+  const float s57 = fadd(gb[5], gb[7]), d57 = fsub(gb[5], gb[7]);
+  const float s68 = fadd(gb[6], gb[8]), d86 = fsub(gb[8], gb[6]);
+  const float m0g = fadd(fadd(fadd(gb[0], s13), fadd(s24, s57)), s68);
+  const float jx = fadd(fadd(d13, d57), d86);
+  const float jy = fsub(fadd(d24, d57), d86);
+  o.rrho = __fdividef(1.0f, o.rho);
+  const float rden = P.remove_Fa ? __fdividef(1.0f, fmad(-0.5f, sdef, o.rho)) : o.rrho;
+  o.ux = fmul(fmad(3.0f, jx, fmul(0.5f, o.fsx)), rden);
+  o.uy = fmul(fmad(3.0f, jy, fmul(0.5f, fadd(o.fsy, o.gy))), rden);
+  o.rx = fmul(P.rho_prime12, gphx);                     // grad rho
+  o.ry = fmul(P.rho_prime12, gphy);
+  o.p = fmad(fmad(o.ux, o.rx, fmul(o.uy, o.ry)), 1.0f / 6.0f, m0g);
+  return o;
+}
+
+// The record S3 needs from S2 (the forced order-parameter fields are set by the caller).
+__device__ __forceinline__ void s2_record(const Phys& P, const S2Out& o, float ph, float mu0, float sdef, Rec& r) {
+  r.phi = ph;
+  r.mu = mu0;
+  r.ux = o.ux;
+  r.uy = o.uy;
+  r.Fx = P.remove_Fa ? fmad(o.ux, sdef, o.fsx) : o.fsx;
+  r.Fy = P.remove_Fa ? fmad(o.uy, sdef, fadd(o.fsy, o.gy)) : fadd(o.fsy, o.gy);
+  r.mrx3 = fmul(-1.0f / 3.0f, o.rx);
+  r.mry3 = fmul(-1.0f / 3.0f, o.ry);
+  const float muv3 = fmad(o.cl, P.mu3_d, P.mu3_B);      // 3 mu(phi)
+  r.og = __fdividef(1.0f, fmad(muv3, o.rrho, 0.5f));    // 1 / tau_g(phi)
+  r.ogr3 = fmul(r.og, fmul(o.rho, 1.0f / 3.0f));
+}
+
+// S3: phi div(u) of the convective Cahn-Hilliard source from u_x rows (xs, x0, xn) and u_y rows
+// (ys, yn): 12 d(ux)/dx = 4 (E - W) + (NE - SW) - (NW - SE), 12 d(uy)/dy = 4 (N - S) + (NE - SW) + (NW - SE).
+__device__ __forceinline__ float phi_div_u(float phi, const float* xs, const float* x0, const float* xn, const float* ys,
+                                           const float* yn) {
+  const float dux = fmad(4.0f, fsub(x0[1], x0[-1]), fsub(fsub(xn[1], xs[-1]), fsub(xn[-1], xs[1])));
+  const float duy = fmad(4.0f, fsub(yn[0], ys[0]), fadd(fsub(yn[1], ys[-1]), fsub(yn[-1], ys[1])));
+  return fmul(phi, fmul(fadd(dux, duy), 1.0f / 12.0f));
+}
+
 // The fused step (MODE_STEP) or the moment evaluation (MODE_MOMENTS) over one tile:
 // columns [x0, x0 + tile_w) x rows [ya, yb) of one simulation.
 //
@@ -601,10 +696,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
 #pragma unroll
       for (int k = 0; k < Q; ++k) fp[k] = dec_pop<ST>(fpr[k], k, g.isf);
       fp[Q] = __uint_as_float(fpr[Q]);
-      const float small =
-          fadd(fp[Q], fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8]))));
       float hi, lo;
-      two_sum(fp[0], small, hi, lo);
+      phi_pair(fp, hi, lo);
       put(o0, a, R_PHI_HI, hi, CK{});
       put(o0, a, R_PHI_LO, lo, CK{});
       if (MODE == MODE_STEP && in_w0 && (IN || a >= ya)) {
@@ -623,17 +716,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         const float* ls = ring + o3 + R_PHI_LO * NT + t;
         const float* l0 = ring + o2 + R_PHI_LO * NT + t;
         const float* ln = ring + o1 + R_PHI_LO * NT + t;
-        const float H = h0[0], L = l0[0];
-        // differences from the centre: exact for neighbouring values of like magnitude; the low
-        // words are tiny and are summed directly
-        const float dax = fadd(fadd(fsub(h0[1], H), fsub(hn[0], H)), fadd(fsub(h0[-1], H), fsub(hs[0], H)));
-        const float ddg = fadd(fadd(fsub(hn[1], H), fsub(hn[-1], H)), fadd(fsub(hs[-1], H), fsub(hs[1], H)));
-        const float lax = fadd(fadd(l0[1], ln[0]), fadd(l0[-1], ls[0]));
-        const float ldg = fadd(fadd(ln[1], ln[-1]), fadd(ls[-1], ls[1]));
-        const float lap6 = fmad(-20.0f, L, fmad(4.0f, fadd(dax, lax), fadd(ddg, ldg)));   // 6 lap(phi)
-        const float ph = fadd(H, L);
-        const float dm = fadd(fsub(H, P.phi_star), L), dp = fadd(fadd(H, P.phi_star), L);
-        put(o2, r, R_MU, fmad(-P.kappa6, lap6, fmul(fmul(fmul(P.four_beta, ph), dm), dp)), CK{});
+        put(o2, r, R_MU, chem_potential(P, hs, h0, hn, ls, l0, ln), CK{});
       }
     }
     // ---- S2: u, p at row a-4 (rows a-5 .. a-3 of phi and mu)
@@ -651,49 +734,23 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         float gphx, gphy, gmx, gmy;                // 12 x the isotropic gradients
         grad12(hs, h0, hn, gphx, gphy);
         grad12(ms, m0, mn, gmx, gmy);
-        const float cl = __saturatef(fmad(ph, P.inv_2phistar, 0.5f));   // clamp((phi + phi*) / (2 phi*))
-        const float rho = fmad(cl, P.drho, P.rho_B);
-        float fsx, fsy;                            // F_s = -phi grad mu, or mu grad phi
-        if (P.fs_mu) {
-          const float mu12 = fmul(m0[0], 1.0f / 12.0f);
-          fsx = fmul(mu12, gphx);
-          fsy = fmul(mu12, gphy);
-        } else {
-          const float mph12 = fmul(ph, -1.0f / 12.0f);
-          fsx = fmul(mph12, gmx);
-          fsy = fmul(mph12, gmy);
-        }
-        const float gy = fmul(-P.gravity, rho);
-        float sdef = 0.0f;
         // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
         auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
-        auto lap6_mu = [&]() {   // 6 lap(mu)
-          return fmad(-20.0f, m0[0], fmad(4.0f, fadd(fadd(m0[1], mn[0]), fadd(m0[-1], ms[0])),
-                                          fadd(fadd(mn[1], mn[-1]), fadd(ms[-1], ms[1]))));
-        };
+        float sdef = 0.0f;
         if (P.remove_Fa || (MODE == MODE_MOMENTS && mo.fax)) {
           if constexpr (SD) {
-            sdef = fadd(fsub(rho, __uint_as_float(spr[0])), __uint_as_float(spr[1]));   // prefetched
+            // this cell's rho (formed as s2_cell forms it) less the prefetched rho of the last step
+            const float rho_ = fmad(__saturatef(fmad(ph, P.inv_2phistar, 0.5f)), P.drho, P.rho_B);
+            sdef = fadd(fsub(rho_, __uint_as_float(spr[0])), __uint_as_float(spr[1]));
           } else {
-            sdef = fmul(P.s_coef6, lap6_mu());
+            sdef = fmul(P.s_coef6, lap6_of(ms, m0, mn));
           }
         }
         float gb[Q];
 #pragma unroll
         for (int k = 0; k < Q; ++k) gb[k] = dec_pop<ST>(gpr[k], Q + k, g.isg);
-        const float s13 = fadd(gb[1], gb[3]), d13 = fsub(gb[1], gb[3]);
-        const float s24 = fadd(gb[2], gb[4]), d24 = fsub(gb[2], gb[4]);
-        const float s57 = fadd(gb[5], gb[7]), d57 = fsub(gb[5], gb[7]);
-        const float s68 = fadd(gb[6], gb[8]), d86 = fsub(gb[8], gb[6]);
-        const float m0g = fadd(fadd(fadd(gb[0], s13), fadd(s24, s57)), s68);
-        const float jx = fadd(fadd(d13, d57), d86);
-        const float jy = fsub(fadd(d24, d57), d86);
-        const float rrho = __fdividef(1.0f, rho);
-        const float rden = P.remove_Fa ? __fdividef(1.0f, fmad(-0.5f, sdef, rho)) : rrho;
-        const float ux = fmul(fmad(3.0f, jx, fmul(0.5f, fsx)), rden);
-        const float uy = fmul(fmad(3.0f, jy, fmul(0.5f, fadd(fsy, gy))), rden);
-        const float rx = fmul(P.rho_prime12, gphx), ry = fmul(P.rho_prime12, gphy);   // grad rho
-        const float p = fmad(fmad(ux, rx, fmul(uy, ry)), 1.0f / 6.0f, m0g);
+        const S2Out s2 = s2_cell(P, ph, gphx, gphy, gmx, gmy, m0[0], sdef, gb);
+        const float rho = s2.rho, ux = s2.ux, uy = s2.uy, p = s2.p;
         put(o4, r, R_P, p, CK{});
         if (MODE == MODE_STEP && (P.ch_conv || SD)) put_u(r, ux, uy, CK{});
         if (MODE == MODE_STEP && SD) {
@@ -718,21 +775,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
 #pragma unroll
             for (int k = 0; k < Q; ++k) sm.g[r & 1][k][t] = gb[k];
           }
-          cur.phi = ph;
-          cur.mu = m0[0];
-          cur.ux = ux;
-          cur.uy = uy;
-          cur.Fx = P.remove_Fa ? fmad(ux, sdef, fsx) : fsx;
-          cur.Fy = P.remove_Fa ? fmad(uy, sdef, fadd(fsy, gy)) : fadd(fsy, gy);
-          cur.mrx3 = fmul(-1.0f / 3.0f, rx);
-          cur.mry3 = fmul(-1.0f / 3.0f, ry);
-          const float muv3 = fmad(cl, P.mu3_d, P.mu3_B);                  // 3 mu(phi)
-          cur.og = __fdividef(1.0f, fmad(muv3, rrho, 0.5f));              // 1 / tau_g(phi)
-          cur.ogr3 = fmul(cur.og, fmul(rho, 1.0f / 3.0f));
+          s2_record(P, s2, ph, m0[0], sdef, cur);
           if constexpr (FF) {
             cur.gx12 = gphx;
             cur.gy12 = gphy;
-            cur.lmu6 = lap6_mu();
+            cur.lmu6 = lap6_of(ms, m0, mn);
           }
         }
       }
@@ -753,12 +800,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
           const float* xs_ = uring + (IN ? uslot(a - 6) : uslot_ck(a - 6)) + t;
           const float* x0_ = uring + uslot(a - 5) + t;
           const float* xn_ = uring + (IN ? uslot(a - 4) : uslot_ck(a - 4)) + t;
-          const float* ys_ = xs_ + NT;
-          const float* yn_ = xn_ + NT;
-          // 12 d(ux)/dx = 4 (E - W) + (NE - SW) - (NW - SE);  12 d(uy)/dy = 4 (N - S) + (NE - SW) + (NW - SE)
-          const float dux = fmad(4.0f, fsub(x0_[1], x0_[-1]), fsub(fsub(xn_[1], xs_[-1]), fsub(xn_[-1], xs_[1])));
-          const float duy = fmad(4.0f, fsub(yn_[0], ys_[0]), fadd(fsub(yn_[1], ys_[-1]), fsub(yn_[-1], ys_[1])));
-          phiD = fmul(prev.phi, fmul(fadd(dux, duy), 1.0f / 12.0f));
+          phiD = phi_div_u(prev.phi, xs_, x0_, xn_, xs_ + NT, xn_ + NT);
         }
         const int rslot = fslot == RING_F - 1 ? 0 : fslot + 1;   // row a-5 == row a+1 (mod 6)
         float f[Q], gb[Q];

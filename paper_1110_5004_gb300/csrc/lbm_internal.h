@@ -27,6 +27,7 @@ struct lbm_sim {
   long long steps = 0;
   long long launches = 0;
   int nt = 128;                        // threads per CTA of the step kernel
+  int kernel = LBM_KERNEL_AUTO;        // step kernel choice (lbm_set_kernel)
   int seg_h = 0;                       // rows per CTA (0: one wave of resident CTAs)
   int sms = 0;                         // multiprocessors of the device
   int occ = 0;                         // resident step CTAs per SM at the current nt
@@ -56,6 +57,12 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst);
 // CTAs (slots = SMs x CTAs per SM) on the device.
 void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, int* n_strips, int* seg_out);
 int tile_occupancy(int nt);
+// The small-grid step kernel (lbm_tile2d.cu): s_form 0 and f_form 0.
+bool tile2d_eligible(const lbm_params& p);
+cudaError_t launch_tile2d(const Phys& P, const Grid& g, cudaStream_t st);
+// Grids of at most this many cells run the small-grid kernel by default.
+constexpr long long SMALL_GRID_CELLS = 1 << 19;
+bool uses_tile2d(const lbm_sim* s);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_step(const Phys& P, const Grid& g, int nt, cudaStream_t st);

@@ -105,13 +105,17 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("kernel", ["rows", "tiles"])
 @pytest.mark.parametrize("nx,ny,bcx,bcy,st,sform,tile", CASES)
-def test_pad_columns_never_touched(lbm, nx, ny, bcx, bcy, st, sform, tile):
+def test_pad_columns_never_touched(lbm, nx, ny, bcx, bcy, st, sform, tile, kernel):
+    if kernel == "tiles" and sform:
+        pytest.skip("the tile kernel runs s_form 0 only")
     w = W.random_small(nx, ny, seed=nx + ny, bc_x=bcx, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0,
                        remove_Fa=1)
     w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=sform))
-    sim = lbm.Sim.from_workload(w, tile=tile, storage=st)
-    ref = lbm.Sim.from_workload(w, tile=tile, storage=st)
+    k = lbm.LBM_KERNEL_ROWS if kernel == "rows" else lbm.LBM_KERNEL_TILES
+    sim = lbm.Sim.from_workload(w, tile=tile, storage=st, kernel=k)
+    ref = lbm.Sim.from_workload(w, tile=tile, storage=st, kernel=k)
     # poison the pads of the current buffer, step once, then those of the other buffer
     for _ in range(2):
         c = sim.checkpoint()

@@ -245,6 +245,44 @@ def test_strip_ending_short_of_a_side_wall(lbm, nx, tile):
     assert_parity(got, ref, w)
 
 
+TILE_CASES = [
+    # nx, ny, bc_x, bc_y, remove_Fa, ch_conservative, fs_form, storage, seed
+    (24, 20, W.PERIODIC, W.PERIODIC, 0, 0, 0, 0, 1),
+    (33, 17, W.PERIODIC, W.WALL, 1, 0, 0, 0, 2),
+    (29, 31, W.WALL, W.WALL, 1, 0, 1, 0, 3),
+    (7, 5, W.PERIODIC, W.PERIODIC, 1, 1, 0, 0, 4),
+    (130, 9, W.WALL, W.PERIODIC, 0, 1, 1, 0, 5),
+    (47, 38, W.WALL, W.WALL, 1, 0, 0, 1, 6),
+    (40, 24, W.PERIODIC, W.WALL, 0, 0, 0, 2, 7),
+    (150, 90, W.PERIODIC, W.WALL, 1, 0, 0, 0, 8),
+]
+
+
+@pytest.mark.parametrize("nx,ny,bcx,bcy,rf,ch,fs,st,seed", TILE_CASES)
+def test_tile_kernel_equals_row_march(lbm, nx, ny, bcx, bcy, rf, ch, fs, st, seed):
+    """The small-grid tile kernel computes every cell bitwise as the row march: the whole state
+    after 40 steps on odd and ragged grids (edge tiles cut by the grid), walls on either axis,
+    both schemes, both Cahn-Hilliard forms, both surface forces and every storage."""
+    import dataclasses
+    w = W.random_small(nx, ny, seed=seed, bc_x=bcx, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0,
+                       remove_Fa=rf)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, ch_conservative=ch, fs_form=fs))
+    rows = lbm.Sim.from_workload(w, storage=st, kernel=lbm.LBM_KERNEL_ROWS)
+    tiles = lbm.Sim.from_workload(w, storage=st, kernel=lbm.LBM_KERNEL_TILES)
+    rows.step(40)
+    tiles.step(40)
+    assert np.array_equal(tiles.checkpoint(), rows.checkpoint())
+
+
+def test_tile_kernel_refused_where_it_does_not_apply(lbm):
+    import dataclasses
+    w = W.random_small(40, 24, seed=3)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, s_form=1))
+    s = lbm.Sim.from_workload(w)
+    with pytest.raises(lbm.LBMError):
+        s.set_kernel(lbm.LBM_KERNEL_TILES)
+
+
 @pytest.mark.parametrize("rf", [0, 1])
 def test_c1_static_droplet(lbm, rf):
     """c1 (128x128 periodic, R = 25, rho 1:0.1): 1e-5 after 200 steps; the full 1000-step run

@@ -223,8 +223,10 @@ def gpu_stream():
 def test_served_results_equal_alone(lbm, solo_cells):
     """Bitwise the results of the same requests run one by one; with solo_cells = 4000 the larger
     requests step alone on the server stream next to the batch of the smaller ones."""
+    import dataclasses
     from paper_1110_5004_gb300 import serve
-    reqs = gpu_stream()
+    # all arrive at once, so that their work overlaps however fast each runs
+    reqs = [dataclasses.replace(r, arrival_s=0.0) for r in gpu_stream()]
     srv = serve.Server(budget_bytes=1 << 34, chunk_steps=64, keep_fields=True, solo_cells=solo_cells)
     served = srv.run(reqs)
     alone = serve.run_plain(reqs, keep_fields=True)
