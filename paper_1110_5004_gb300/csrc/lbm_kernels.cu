@@ -16,6 +16,12 @@ template <int NT, int MODE, int ST, bool SD, bool FF>
 __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 512 / NT) k_tiles(Phys P, Grid g, MomentOut mo) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Smem<NT>& sm = *reinterpret_cast<Smem<NT>*>(smem_raw);
+  if (MODE == MODE_STEP) {
+    // launched as a programmatic dependent of the previous step: wait until that grid has
+    // completed and its stores are visible, then let the next step's launch proceed
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  }
   const int strip = blockIdx.x % g.n_strips;
   const int seg = blockIdx.x / g.n_strips;
   run_tile<NT, MODE, ST, SD, FF>(P, g, mo, strip, seg, sm);
@@ -32,8 +38,22 @@ static cudaError_t launch_sd(const Phys& P, const Grid& g, const MomentOut& mo, 
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_tiles<NT, MODE, ST, SD, FF><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
-  return cudaGetLastError();
+  if (MODE != MODE_STEP) {
+    k_tiles<NT, MODE, ST, SD, FF><<<n_tiles(g), NT, sizeof(Smem<NT>), st>>>(P, g, mo);
+    return cudaGetLastError();
+  }
+  // consecutive steps overlap their launches (programmatic dependent launch)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(n_tiles(g));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = sizeof(Smem<NT>);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tiles<NT, MODE, ST, SD, FF>, P, g, mo);
 }
 
 template <int NT, int MODE, int ST>
