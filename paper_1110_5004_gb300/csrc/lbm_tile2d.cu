@@ -206,8 +206,10 @@ static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_
 }
 
 // 16 x 8 cells per CTA of 256 threads: every frame cell of S0 in two rounds, one for S1 and S2.
-// Measured against 16 x 8 / 128 threads, 8 x 8 / 64 and 128, 16 x 16 / 256 and 32 x 8 / 256 on
-// 128^2, 300 x 150, 150 x 450, 256 x 1024 and 512^2 grids: fastest or within 3 % on each.
+// Measured against 16 x 8 / 128 and 384 threads, 16 x 4 / 256, 8 x 8 / 64, 128 and 256,
+// 16 x 16 / 256, 32 x 4 / 256 and 32 x 8 / 256 on 128^2, 300 x 150, 150 x 450, 256 x 1024 and
+// 512^2 grids: fastest or within 3 % on each but 300 x 150, where 16 x 8 / 384 is 11 % faster and
+// every other grid 1-20 % slower.
 template <int ST>
 static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, cudaStream_t st) {
   return launch_tile2d_shape<ST, 16, 8, 256>(P, g, st);

@@ -219,10 +219,10 @@ def gpu_stream():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("solo_cells", [1 << 20, 4000])
+@pytest.mark.parametrize("solo_cells", [1 << 20, 4000, 0])
 def test_served_results_equal_alone(lbm, solo_cells):
-    """Bitwise the results of the same requests run one by one; with solo_cells = 4000 the larger
-    requests step alone on the server stream next to the batch of the smaller ones."""
+    """Bitwise the results of the same requests run one by one: all batched (1M), the larger ones
+    alone on streams of their own next to the batch of the smaller ones (4000), all alone (0)."""
     import dataclasses
     from paper_1110_5004_gb300 import serve
     # all arrive at once, so that their work overlaps however fast each runs
