@@ -56,6 +56,7 @@ extern "C" {
                               else the row march */
 #define LBM_KERNEL_ROWS 1  /* strips marching rows: every configuration */
 #define LBM_KERNEL_TILES 2 /* 2-D tiles in four shared-memory passes: s_form 0, f_form 0 */
+#define LBM_KERNEL_RESIDENT 3 /* the 2-D tiles kept resident: one launch per lbm_step call */
 
 /* return codes */
 #define LBM_OK 0
@@ -229,12 +230,31 @@ LBM_API int lbm_set_stream(lbm_sim* sim, void* cuda_stream);
 LBM_API int lbm_set_tile(lbm_sim* sim, int threads, int seg_rows);
 
 /* Step kernel of the simulation (no counterpart in the paper; both kernels compute every cell
- * bitwise alike): LBM_KERNEL_AUTO (default), LBM_KERNEL_ROWS or LBM_KERNEL_TILES.  The row march
+ * bitwise alike): LBM_KERNEL_AUTO (default), LBM_KERNEL_ROWS, LBM_KERNEL_TILES or
+ * LBM_KERNEL_RESIDENT.  The row march
  * streams large grids at the memory system's pace; on small grids its per-segment pipeline is
  * latency-bound, and the tile kernel (one load round and four short passes per step) is faster.
- * LBM_KERNEL_TILES needs s_form 0 and f_form 0 (else LBM_ERR_INVALID_ARG).  Takes effect at the
+ * LBM_KERNEL_TILES and LBM_KERNEL_RESIDENT need s_form 0 and f_form 0 (else
+ * LBM_ERR_INVALID_ARG).  Takes effect at the
  * next lbm_step; batches always run their own kernel. */
 LBM_API int lbm_set_kernel(lbm_sim* sim, int kernel);
+/* LBM_KERNEL_RESIDENT (same scope as LBM_KERNEL_TILES) runs lbm_step(sim, n >= 2) as ONE launch
+ * whose CTAs stay on the device for all n steps (a cooperative launch of at most one wave, each
+ * CTA stepping its tiles in turn).  Before a step, a tile waits only until the tiles within 4
+ * cells of it (the farthest a step reads) have finished the previous step; the result is bitwise
+ * that of LBM_KERNEL_TILES.  n = 1 runs the tile kernel.
+ *
+ * lbm_set_wait_limit: every such wait gives up after timeout_ns nanoseconds (default 1e9, > 0);
+ *   the launch then ends early and leaves the state undefined, later resident launches do
+ *   nothing, and the next lbm_step_status or lbm_diagnostics returns LBM_ERR_TIMEOUT (which
+ *   re-arms the waits; lbm_init_fields or lbm_restore then gives a defined state again).
+ *   hold_tile >= 0 is a test hook: that tile (row-major 16 x 8 tiles) never announces a finished
+ *   step, so the waits of its neighbours run out; -1 (default) disables it.
+ * lbm_step_status: synchronises the simulation's stream; LBM_ERR_TIMEOUT if a resident launch
+ *   gave up since the status was last read, else LBM_OK.
+ * Errors: LBM_ERR_INVALID_ARG for a NULL sim or timeout_ns <= 0; LBM_ERR_CUDA. */
+LBM_API int lbm_set_wait_limit(lbm_sim* sim, long long timeout_ns, int hold_tile);
+LBM_API int lbm_step_status(lbm_sim* sim);
 
 /* Kernel launches issued by this simulation since creation (step, init, moments,
  * reductions). */

@@ -12,12 +12,13 @@ import numpy as np
 
 from . import _lib
 from ._lib import (LBM_BF16_DEV, LBM_ERR_BUDGET, LBM_ERR_DIVERGED, LBM_FP16_DEV, LBM_FP32,
-                   LBM_KERNEL_AUTO, LBM_KERNEL_ROWS, LBM_KERNEL_TILES, LBM_PERIODIC, LBM_WALL,
+                   LBM_KERNEL_AUTO, LBM_KERNEL_RESIDENT, LBM_KERNEL_ROWS, LBM_KERNEL_TILES, LBM_PERIODIC, LBM_WALL,
                    LBMError, lbm_diag, lbm_params)
 
 __all__ = ["Sim", "Batch", "LBMError", "params_from_physical", "lbm_params", "LBM_FP32",
            "LBM_FP16_DEV", "LBM_BF16_DEV", "LBM_PERIODIC", "LBM_WALL", "LBM_ERR_DIVERGED",
-           "LBM_ERR_BUDGET", "LBM_KERNEL_AUTO", "LBM_KERNEL_ROWS", "LBM_KERNEL_TILES", "device_bytes"]
+           "LBM_ERR_BUDGET", "LBM_KERNEL_AUTO", "LBM_KERNEL_ROWS", "LBM_KERNEL_TILES", "LBM_KERNEL_RESIDENT",
+           "device_bytes"]
 
 
 def lib():
@@ -121,9 +122,19 @@ class Sim:
         _lib.check(lib().lbm_set_tile(self._h, int(threads), int(seg_rows)))
 
     def set_kernel(self, kernel):
-        """Step kernel: LBM_KERNEL_AUTO, LBM_KERNEL_ROWS or LBM_KERNEL_TILES (bitwise the same
-        results; the tile kernel needs s_form 0 and f_form 0)."""
+        """Step kernel: LBM_KERNEL_AUTO, LBM_KERNEL_ROWS, LBM_KERNEL_TILES or LBM_KERNEL_RESIDENT
+        (bitwise the same results; the tile kernels need s_form 0 and f_form 0)."""
         _lib.check(lib().lbm_set_kernel(self._h, int(kernel)))
+
+    def set_wait_limit(self, timeout_ns, hold_tile=-1):
+        """lbm_set_wait_limit: bound of the resident kernel's waits; hold_tile >= 0 makes that
+        tile never announce a finished step (the test of the bound)."""
+        _lib.check(lib().lbm_set_wait_limit(self._h, int(timeout_ns), int(hold_tile)))
+
+    def step_status(self):
+        """lbm_step_status: LBM_OK (0), or LBM_ERR_TIMEOUT if a resident launch gave up since the
+        last read (returned, not raised)."""
+        return int(lib().lbm_step_status(self._h))
 
     def set_stream(self, stream):
         _lib.check(lib().lbm_set_stream(self._h, _stream_handle(stream)))

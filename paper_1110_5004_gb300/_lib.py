@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "liblbm.so")
 
 LBM_PERIODIC, LBM_WALL = 0, 1
 LBM_FP32, LBM_FP16_DEV, LBM_BF16_DEV = 0, 1, 2
-LBM_KERNEL_AUTO, LBM_KERNEL_ROWS, LBM_KERNEL_TILES = 0, 1, 2
+LBM_KERNEL_AUTO, LBM_KERNEL_ROWS, LBM_KERNEL_TILES, LBM_KERNEL_RESIDENT = 0, 1, 2, 3
 LBM_OK = 0
 LBM_ERR_INVALID_ARG, LBM_ERR_OOM, LBM_ERR_BUDGET, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_CUDA = \
     -1, -2, -3, -4, -5, -6
@@ -26,7 +26,7 @@ EXPORTS = (
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
     "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
     "lbm_checkpoint", "lbm_restore", "lbm_sim_device_bytes", "lbm_init_fields_packed", "lbm_moments_packed",
-    "lbm_set_kernel",
+    "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_status",
 )
 
 
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
         "lbm_set_stream": (ip, [vp, vp]),
         "lbm_set_tile": (ip, [vp, ip, ip]),
         "lbm_set_kernel": (ip, [vp, ip]),
+        "lbm_set_wait_limit": (ip, [vp, ctypes.c_longlong, ip]),
+        "lbm_step_status": (ip, [vp]),
         "lbm_launch_count": (ctypes.c_longlong, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ip]),
         "lbm_last_error": (ctypes.c_char_p, []),

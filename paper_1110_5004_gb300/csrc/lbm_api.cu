@@ -101,7 +101,8 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
 
 bool uses_tile2d(const lbm_sim* s) {
   if (s->kernel == LBM_KERNEL_ROWS || !tile2d_eligible(s->params)) return false;
-  return s->kernel == LBM_KERNEL_TILES || (long long)s->nx * s->ny <= SMALL_GRID_CELLS;
+  return s->kernel == LBM_KERNEL_TILES || s->kernel == LBM_KERNEL_RESIDENT ||
+         (long long)s->nx * s->ny <= SMALL_GRID_CELLS;
 }
 
 static int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
@@ -239,6 +240,12 @@ static cudaError_t copy_field(const lbm_sim* s, float* dst, size_t dpitch, const
   return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row, s->ny, kind, s->stream);
 }
 
+// A new state re-arms the resident kernel's waits: a launch that gave up is forgotten.
+static cudaError_t rearm_resident(lbm_sim* s) {
+  s->res_used = false;
+  return resident_reset(s);
+}
+
 static int upload_field(lbm_sim* s, int k, const float* src) {
   float* dst = s->fields + (long long)k * s->plane;
   cudaError_t e;
@@ -261,6 +268,7 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
   cudaError_t e = cudaEventRecord(s->uploaded, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields record");
   e = launch_init(s, s->stream);
+  if (e == cudaSuccess) e = rearm_resident(s);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields launch");
   s->launches += s->params.s_form ? 3 : 2;
   s->steps = 0;
@@ -302,6 +310,7 @@ int lbm_init_fields_packed(lbm_sim* s, const float* fields) {
   if (e == cudaSuccess) e = cudaEventRecord(s->uploaded, s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields_packed upload");
   e = launch_init(s, s->stream);
+  if (e == cudaSuccess) e = rearm_resident(s);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields_packed launch");
   s->launches += s->params.s_form ? 3 : 2;
   s->steps = 0;
@@ -310,10 +319,39 @@ int lbm_init_fields_packed(lbm_sim* s, const float* fields) {
   return LBM_OK;
 }
 
+// Status of the resident launches since the last read (synchronising the stream when one ran;
+// `sync` forces the synchronisation).  A launch that gave up returns LBM_ERR_TIMEOUT and re-arms
+// the waits (flags and status zeroed).
+static int read_resident_status(lbm_sim* s, bool sync) {
+  cudaError_t e = cudaSuccess;
+  if (!s->res_used) {
+    if (sync && (e = cudaStreamSynchronize(s->stream)) != cudaSuccess) return cuda_fail(e, "stream synchronise");
+    return LBM_OK;
+  }
+  unsigned int st = 0;
+  e = cudaMemcpyAsync(&st, s->res_mem + resident_tiles(s->nx, s->ny), sizeof st, cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(e, "status copy");
+  s->res_used = false;
+  if (st == 0) return LBM_OK;
+  if ((e = resident_reset(s)) != cudaSuccess) return cuda_fail(e, "status reset");
+  set_error("a wait of the resident step kernel ran out (%lld ns); the state is undefined", s->res_timeout_ns);
+  return LBM_ERR_TIMEOUT;
+}
+
 int lbm_step(lbm_sim* s, int n) {
   Range range_("lbm_step");
   if (!s || n < 0) return set_error("invalid sim or step count"), LBM_ERR_INVALID_ARG;
   if (s->batch) return set_error("simulation is a batch member; step it through its batch"), LBM_ERR_INVALID_ARG;
+  if (n >= 2 && s->kernel == LBM_KERNEL_RESIDENT) {
+    Grid g = make_grid(s, s->buf[s->cur], s->buf[s->cur ^ 1]);
+    cudaError_t e = launch_resident(s, g, n);
+    if (e != cudaSuccess) return cuda_fail(e, "lbm_step resident launch");
+    s->cur ^= n & 1;
+    s->steps += n;
+    s->launches++;
+    return LBM_OK;
+  }
   const bool tiles = uses_tile2d(s);
   for (int i = 0; i < n; ++i) {
     Grid g = make_grid(s, s->buf[s->cur], s->buf[s->cur ^ 1]);
@@ -432,8 +470,8 @@ int lbm_diagnostics(lbm_sim* s, lbm_diag* out) {
   s->launches += 2;
   e = cudaMemcpyAsync(&s->h_diag, s->red + (long long)s->ny * DIAG_PARTIALS, sizeof(lbm_diag),
                       cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "diagnostics copy");
+  if ((rc = read_resident_status(s, true)) != LBM_OK) return rc;
   *out = s->h_diag;
   if (!out->finite) {
     set_error("simulation diverged (non-finite state) at step %lld", out->step);
@@ -446,7 +484,8 @@ int lbm_destroy(lbm_sim* s) {
   if (!s) return LBM_OK;
   if (s->stream || s->buf[0]) cudaStreamSynchronize(s->stream);
   // back to the pool, ordered on the stream: no device-wide synchronisation
-  for (void* p : {s->buf[0], s->buf[1], static_cast<void*>(s->fields), static_cast<void*>(s->red)})
+  for (void* p : {s->buf[0], s->buf[1], static_cast<void*>(s->fields), static_cast<void*>(s->red),
+                  static_cast<void*>(s->res_mem)})
     if (p) cudaFreeAsync(p, s->stream);
   if (s->uploaded) cudaEventDestroy(s->uploaded);
   delete s;
@@ -520,6 +559,7 @@ int lbm_restore(lbm_sim* s, const void* buf, size_t bytes) {
   if (bytes < sizeof(h) + h.payload) return set_error("checkpoint truncated"), LBM_ERR_INVALID_ARG;
   e = cudaMemcpyAsync(s->buf[s->cur], static_cast<const char*>(buf) + sizeof(h), h.payload,
                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = rearm_resident(s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_restore copy");
   s->steps = h.steps;
@@ -550,12 +590,25 @@ int lbm_set_tile(lbm_sim* s, int threads, int seg_rows) {
 
 int lbm_set_kernel(lbm_sim* s, int kernel) {
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
-  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_ROWS && kernel != LBM_KERNEL_TILES)
-    return set_error("kernel must be LBM_KERNEL_AUTO, LBM_KERNEL_ROWS or LBM_KERNEL_TILES"), LBM_ERR_INVALID_ARG;
-  if (kernel == LBM_KERNEL_TILES && !tile2d_eligible(s->params))
-    return set_error("the tile kernel needs s_form 0 and f_form 0"), LBM_ERR_INVALID_ARG;
+  if (kernel != LBM_KERNEL_AUTO && kernel != LBM_KERNEL_ROWS && kernel != LBM_KERNEL_TILES &&
+      kernel != LBM_KERNEL_RESIDENT)
+    return set_error("kernel must be LBM_KERNEL_AUTO, _ROWS, _TILES or _RESIDENT"), LBM_ERR_INVALID_ARG;
+  if ((kernel == LBM_KERNEL_TILES || kernel == LBM_KERNEL_RESIDENT) && !tile2d_eligible(s->params))
+    return set_error("the tile kernels need s_form 0 and f_form 0"), LBM_ERR_INVALID_ARG;
   s->kernel = kernel;
   return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_sim* s, long long timeout_ns, int hold_tile) {
+  if (!s || timeout_ns <= 0) return set_error("invalid sim or timeout"), LBM_ERR_INVALID_ARG;
+  s->res_timeout_ns = timeout_ns;
+  s->res_hold = hold_tile < 0 ? -1 : hold_tile;
+  return LBM_OK;
+}
+
+int lbm_step_status(lbm_sim* s) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  return read_resident_status(s, true);
 }
 
 long long lbm_launch_count(const lbm_sim* s) { return s ? s->launches : -1; }

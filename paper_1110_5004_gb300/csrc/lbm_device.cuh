@@ -215,12 +215,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // Population a (0..8 f, 9..17 gbar, 18 f_0lo) of the cell at byte offsets c, as stored bits (a
 // float, or a 16-bit value in the low half), and their decoding.  A prefetch keeps the bits and
 // decodes them where they are used, so that the conversion does not wait for the load at the
-// point of issue.
-template <int ST>
+// point of issue.  COH: a kernel that reads state other CTAs write during the same launch loads
+// through L2 only (ld.global.cg, ordered by the memory model); every other kernel takes the
+// read-only path.
+template <int ST, bool COH = false>
 __device__ __forceinline__ unsigned int ld_raw(const void* __restrict__ base, int a, CellB c) {
   const char* p = static_cast<const char*>(base) + plane_off<ST>(a);
-  if (ST == ST_FP32 || a == 0) return __float_as_uint(__ldg(reinterpret_cast<const float*>(p + c.b4)));
-  return __ldg(reinterpret_cast<const unsigned short*>(p + c.b2));
+  if (ST == ST_FP32 || a == 0) {
+    const float* q = reinterpret_cast<const float*>(p + c.b4);
+    return __float_as_uint(COH ? __ldcg(q) : __ldg(q));
+  }
+  const unsigned short* q = reinterpret_cast<const unsigned short*>(p + c.b2);
+  return COH ? __ldcg(q) : __ldg(q);
 }
 
 template <int ST>
@@ -247,14 +253,14 @@ __device__ __forceinline__ void st_pop(void* __restrict__ base, int a, CellB c, 
 // bits (decode with dec_pop at plane FIRST + a):
 // v[a] = P*_a(x - e_a), or P*_opp(a)(x) when x - e_a lies beyond a wall (half-way bounce-back).
 // Cells with no wall neighbour take the branch-free path.
-template <int ST, int FIRST>
+template <int ST, int FIRST, bool COH = false>
 __device__ __forceinline__ void gather9(const void* __restrict__ src, const ColNb& c, const RowNb& r, unsigned int v[Q]) {
   if (!(c.wl | c.wr | r.wb | r.wt)) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
       const CellB sx = cx(a) == 1 ? c.cm : (cx(a) == -1 ? c.cq : c.c0);
       const int sr = cy(a) == 1 ? r.bm : (cy(a) == -1 ? r.bq : r.b0);
-      v[a] = ld_raw<ST>(src, FIRST + a, cell_at(sr, sx));
+      v[a] = ld_raw<ST, COH>(src, FIRST + a, cell_at(sr, sx));
     }
   } else {
 #pragma unroll
@@ -263,7 +269,7 @@ __device__ __forceinline__ void gather9(const void* __restrict__ src, const ColN
       const bool hit = (ex == 1 && c.wl) || (ex == -1 && c.wr) || (ey == 1 && r.wb) || (ey == -1 && r.wt);
       const CellB sx = ex == 1 ? c.cm : (ex == -1 ? c.cq : c.c0);
       const int sr = ey == 1 ? r.bm : (ey == -1 ? r.bq : r.b0);
-      v[a] = hit ? ld_raw<ST>(src, FIRST + opp(a), cell_at(r.b0, c.c0)) : ld_raw<ST>(src, FIRST + a, cell_at(sr, sx));
+      v[a] = hit ? ld_raw<ST, COH>(src, FIRST + opp(a), cell_at(r.b0, c.c0)) : ld_raw<ST, COH>(src, FIRST + a, cell_at(sr, sx));
     }
   }
 }

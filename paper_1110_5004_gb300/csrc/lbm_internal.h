@@ -32,6 +32,13 @@ struct lbm_sim {
   int sms = 0;                         // multiprocessors of the device
   int occ = 0;                         // resident step CTAs per SM at the current nt
   float sf = 1.0f, sg = 1.0f;          // 16-bit storage scales of the f and gbar planes
+  // resident tile kernel (lbm_tile2d.cu): per-tile step flags, the status word and the reach
+  // table in one stream-ordered allocation made at first use
+  unsigned int* res_mem = nullptr;
+  unsigned int res_base = 0;           // flag value of every tile between launches
+  long long res_timeout_ns = 1000000000LL;
+  int res_hold = -1;                   // test hook: this tile never announces a finished step
+  bool res_used = false;               // a resident launch ran since the status was last read
   lbm_batch* batch = nullptr;
 };
 
@@ -63,6 +70,11 @@ cudaError_t launch_tile2d(const Phys& P, const Grid& g, cudaStream_t st);
 // Grids of at most this many cells run the small-grid kernel by default.
 constexpr long long SMALL_GRID_CELLS = 1 << 19;
 bool uses_tile2d(const lbm_sim* s);
+// The resident form: one launch of n >= 2 steps (flags and reach table prepared on first use).
+int resident_tiles(int nx, int ny);
+cudaError_t resident_prepare(lbm_sim* s);
+cudaError_t resident_reset(lbm_sim* s);
+cudaError_t launch_resident(lbm_sim* s, const Grid& g, int n);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_step(const Phys& P, const Grid& g, int nt, cudaStream_t st);

@@ -13,6 +13,8 @@
 // position, as in the row march, so the state is bitwise the one the row march computes.
 // Scope: s by Eq. 5 (s_form 0) and the mu-term order-parameter equilibrium (f_form 0), any storage
 // and boundaries; other configurations run the row march.
+#include <vector>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -25,14 +27,14 @@ struct Smem2D {
   float gb[Q][TY][TX];     // their pulled gbar populations
 };
 
-template <int ST, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
+// One step of tile `tile` (row-major over tiles_x columns of tiles) from g.src into g.dst.  COH:
+// population loads through L2 only, for a launch in which other CTAs write the state it reads.
+template <int ST, int TX, int TY, int NT, bool COH>
+__device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int tiles_x, int tile, Smem2D<TX, TY>& sm) {
   using S = Smem2D<TX, TY>;
   constexpr int FW = S::FW, FH = S::FH;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S& sm = *reinterpret_cast<S*>(smem_raw);
   const int t = threadIdx.x;
-  const int x0 = (blockIdx.x % tiles_x) * TX, y0 = (blockIdx.x / tiles_x) * TY;
+  const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
   const bool xwall = g.bc_x == BC_WALL, ywall = g.bc_y == BC_WALL;
 
   // frame position (i, j) <-> logical cell (x0 - 3 + i, y0 - 3 + j)
@@ -53,12 +55,6 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
     cn = make_col<ST>(wrap1(x, g.nx), g);
     rn = make_row(wrap1(y, g.ny), g);
   };
-  // Launched as a programmatic dependent of the previous step: wait until that grid has
-  // completed and its stores are visible, then let the next step's grid be scheduled, so that
-  // its launch overlaps this one instead of following it.
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-
   // Every population load of this thread is issued first, all at once: f of its S0 cells, gbar
   // of its S2 cells and f of its S3 cell; the passes then wait on the loads they use.
   constexpr int C0 = (FW * FH + NT - 1) / NT, C2 = ((FW - 4) * (FH - 4) + NT - 1) / NT, C3 = (TX * TY + NT - 1) / NT;
@@ -70,8 +66,8 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
       ColNb cn;
       RowNb rn;
       nbr(x, y, cn, rn);
-      gather9<ST, 0>(g.src, cn, rn, f0raw[c]);
-      f0raw[c][Q] = ST == ST_FP32 ? ld_raw<ST>(g.src, PLANE_F0LO, cell_at(rn.b0, cn.c0)) : 0u;
+      gather9<ST, 0, COH>(g.src, cn, rn, f0raw[c]);
+      f0raw[c][Q] = ST == ST_FP32 ? ld_raw<ST, COH>(g.src, PLANE_F0LO, cell_at(rn.b0, cn.c0)) : 0u;
     }
   }
 #pragma unroll
@@ -81,7 +77,7 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
       ColNb cn;
       RowNb rn;
       nbr(x, y, cn, rn);
-      gather9<ST, Q>(g.src, cn, rn, g2raw[c]);
+      gather9<ST, Q, COH>(g.src, cn, rn, g2raw[c]);
     }
   }
 #pragma unroll
@@ -91,7 +87,7 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
       ColNb cn;
       RowNb rn;
       nbr(x, y, cn, rn);
-      gather9<ST, 0>(g.src, cn, rn, f3raw[c]);   // the collision's f populations
+      gather9<ST, 0, COH>(g.src, cn, rn, f3raw[c]);   // the collision's f populations
     }
   }
 
@@ -183,6 +179,17 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
 }
 
 template <int ST, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // Launched as a programmatic dependent of the previous step: wait until that grid has
+  // completed and its stores are visible, then let the next step's grid be scheduled, so that
+  // its launch overlaps this one instead of following it.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  tile2d_step<ST, TX, TY, NT, false>(P, g, tiles_x, blockIdx.x, *reinterpret_cast<Smem2D<TX, TY>*>(smem_raw));
+}
+
+template <int ST, int TX, int TY, int NT>
 static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_t st) {
   using S = Smem2D<TX, TY>;
   static bool attr_set = false;   // one GPU per process
@@ -210,12 +217,226 @@ static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_
 // 16 x 16 / 256, 32 x 4 / 256 and 32 x 8 / 256 on 128^2, 300 x 150, 150 x 450, 256 x 1024 and
 // 512^2 grids: fastest or within 3 % on each but 300 x 150, where 16 x 8 / 384 is 11 % faster and
 // every other grid 1-20 % slower.
+constexpr int T2D_TX = 16, T2D_TY = 8, T2D_NT = 256;
+
 template <int ST>
 static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, cudaStream_t st) {
-  return launch_tile2d_shape<ST, 16, 8, 256>(P, g, st);
+  return launch_tile2d_shape<ST, T2D_TX, T2D_TY, T2D_NT>(P, g, st);
+}
+
+// ---- Resident form: one launch advances n steps.  Every CTA stays on the device and steps its
+// tiles (tile = blockIdx.x, + gridDim.x, ...); before a step a tile waits only until the tiles
+// within its reach have finished the previous step, which also means they have read what the
+// step overwrites.  A step of a tile reads cells up to REACH away in x and y (the 3-cell halo of
+// S0 and the pull), so its reach is the tiles owning a cell of the tile grown by REACH.  The
+// waits cannot deadlock: a CTA takes its tiles in order, step by step, so the unfinished tile of
+// the lowest step always has every tile it waits for done.  Every wait is bounded: after
+// timeout_ns it raises the status word and the launch ends.
+constexpr int REACH = 4;
+constexpr int NB_MAX = 16;   // a tile grown by 4 meets at most 4 x 4 tiles of 16 x 8 (a ragged one included)
+
+struct Resident {
+  unsigned int* flags;    // per tile: base + steps it has finished in this launch
+  unsigned int* status;   // 0, or RES_GAVE_UP after a wait ran out (cleared by the host)
+  const int* reach;       // per tile NB_MAX tile indices within reach, itself excluded, -1 padded
+  unsigned int base;      // flag value of every tile when the launch starts
+  int nsteps, ntiles;
+  long long timeout_ns;
+  int hold_tile;          // this tile never announces a finished step (-1: none)
+};
+constexpr unsigned int RES_GAVE_UP = 1u;
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until every tile within reach of `tile` has finished `need` steps of this launch; lane i
+// of warp 0 watches neighbour i.  False (in every thread) when the launch gives up.
+__device__ __forceinline__ bool wait_reach(const Resident& R, int tile, int need) {
+  bool quit = false;
+  if (threadIdx.x < NB_MAX) {
+    const int n = __ldg(R.reach + tile * NB_MAX + threadIdx.x);
+    if (n >= 0) {
+      const unsigned int* f = R.flags + n;
+      const unsigned int want = R.base + (unsigned int)need;
+      if ((int)(ld_acquire(f) - want) < 0) {
+        const unsigned long long t0 = global_ns();
+        for (;;) {
+          __nanosleep(32);
+          if ((int)(ld_acquire(f) - want) >= 0) break;
+          if (ld_acquire(R.status) != 0u) {   // another tile gave up: so does this launch
+            quit = true;
+            break;
+          }
+          if (global_ns() - t0 > (unsigned long long)R.timeout_ns) {
+            atomicCAS(R.status, 0u, RES_GAVE_UP);
+            quit = true;
+            break;
+          }
+        }
+      }
+    }
+  }
+  return !__syncthreads_or(quit);
+}
+
+template <int ST, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) k_tile2d_resident(Phys P, Grid g, int tiles_x, Resident R) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Smem2D<TX, TY>& sm = *reinterpret_cast<Smem2D<TX, TY>*>(smem_raw);
+  // a launch that gave up leaves the state undefined: later launches do nothing until the host
+  // has read the status and reset it
+  if (__syncthreads_or(threadIdx.x == 0 && ld_acquire(R.status) != 0u)) return;
+  Grid h = g;   // odd steps run back from dst into src
+  h.src = g.dst;
+  h.dst = const_cast<void*>(g.src);
+  for (int s = 0; s < R.nsteps; ++s) {
+    for (int tile = blockIdx.x; tile < R.ntiles; tile += gridDim.x) {
+      if (s > 0 && !wait_reach(R, tile, s)) return;
+      tile2d_step<ST, TX, TY, NT, true>(P, (s & 1) ? h : g, tiles_x, tile, sm);
+      __syncthreads();   // every store of the tile issued (and shared memory free for the next)
+      if (threadIdx.x == 0 && tile != R.hold_tile) {
+        __threadfence();
+        st_release(R.flags + tile, R.base + (unsigned int)(s + 1));
+      }
+    }
+  }
+}
+
+// Tiles within reach of each tile (itself excluded), NB_MAX per tile, -1 padded.
+static bool reach_table(const Grid& g, int tx_n, int ty_n, int* out) {
+  for (int ty = 0; ty < ty_n; ++ty)
+    for (int tx = 0; tx < tx_n; ++tx) {
+      int xs[NB_MAX], ys[NB_MAX], nxs = 0, nys = 0;
+      const int x0 = tx * T2D_TX, x1 = (x0 + T2D_TX < g.nx ? x0 + T2D_TX : g.nx) - 1;
+      const int y0 = ty * T2D_TY, y1 = (y0 + T2D_TY < g.ny ? y0 + T2D_TY : g.ny) - 1;
+      for (int c = x0 - REACH; c <= x1 + REACH; ++c) {
+        if (g.bc_x == BC_WALL && (c < 0 || c >= g.nx)) continue;
+        const int k = ((c % g.nx) + g.nx) % g.nx / T2D_TX;
+        bool seen = false;
+        for (int i = 0; i < nxs; ++i) seen |= xs[i] == k;
+        if (!seen) {
+          if (nxs == NB_MAX) return false;
+          xs[nxs++] = k;
+        }
+      }
+      for (int c = y0 - REACH; c <= y1 + REACH; ++c) {
+        if (g.bc_y == BC_WALL && (c < 0 || c >= g.ny)) continue;
+        const int k = ((c % g.ny) + g.ny) % g.ny / T2D_TY;
+        bool seen = false;
+        for (int i = 0; i < nys; ++i) seen |= ys[i] == k;
+        if (!seen) {
+          if (nys == NB_MAX) return false;
+          ys[nys++] = k;
+        }
+      }
+      int* row = out + (size_t)(ty * tx_n + tx) * NB_MAX;
+      int n = 0;
+      for (int i = 0; i < NB_MAX; ++i) row[i] = -1;
+      for (int j = 0; j < nys; ++j)
+        for (int i = 0; i < nxs; ++i) {
+          const int k = ys[j] * tx_n + xs[i];
+          if (k == ty * tx_n + tx) continue;
+          if (n == NB_MAX) return false;
+          row[n++] = k;
+        }
+    }
+  return true;
+}
+
+template <int ST>
+static cudaError_t launch_resident_st(lbm_sim* s, const Grid& g, int n) {
+  using S = Smem2D<T2D_TX, T2D_TY>;
+  auto* k = k_tile2d_resident<ST, T2D_TX, T2D_TY, T2D_NT>;
+  static int occ = 0;   // one GPU per process
+  if (occ == 0) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(S));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, T2D_NT, sizeof(S));
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+  }
+  const int tx = (g.nx + T2D_TX - 1) / T2D_TX, ty = (g.ny + T2D_TY - 1) / T2D_TY, nt = tx * ty;
+  const int slots = occ * s->sms;
+  Resident R{};
+  R.flags = s->res_mem;
+  R.status = s->res_mem + nt;
+  R.reach = reinterpret_cast<const int*>(s->res_mem + nt + 1);
+  R.base = s->res_base;
+  R.nsteps = n;
+  R.ntiles = nt;
+  R.timeout_ns = s->res_timeout_ns;
+  R.hold_tile = s->res_hold;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(nt < slots ? nt : slots);
+  cfg.blockDim = dim3(T2D_NT);
+  cfg.dynamicSmemBytes = sizeof(S);
+  cfg.stream = s->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;   // every CTA resident at once: the waits need it
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, s->phys, g, tx, R);
 }
 
 bool tile2d_eligible(const lbm_params& p) { return p.s_form == 0 && p.f_form == 0; }
+
+int resident_tiles(int nx, int ny) {
+  return ((nx + T2D_TX - 1) / T2D_TX) * ((ny + T2D_TY - 1) / T2D_TY);
+}
+
+// Flags, status word and reach table of the simulation, allocated on first use and zeroed.
+cudaError_t resident_prepare(lbm_sim* s) {
+  if (s->res_mem) return cudaSuccess;
+  const int nt = resident_tiles(s->nx, s->ny);
+  const size_t words = (size_t)nt + 1 + (size_t)nt * NB_MAX;
+  std::vector<int> host((size_t)nt * NB_MAX);
+  const Grid g = make_grid(s, nullptr, nullptr);
+  if (!reach_table(g, (s->nx + T2D_TX - 1) / T2D_TX, (s->ny + T2D_TY - 1) / T2D_TY, host.data()))
+    return cudaErrorInvalidValue;   // cannot happen for 16 x 8 tiles and a reach of 4
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, words * sizeof(unsigned int), s->stream);
+  if (e != cudaSuccess) return e;
+  s->res_mem = static_cast<unsigned int*>(p);
+  e = cudaMemsetAsync(s->res_mem, 0, ((size_t)nt + 1) * sizeof(unsigned int), s->stream);
+  if (e == cudaSuccess)   // pageable source: staged before the call returns
+    e = cudaMemcpyAsync(s->res_mem + nt + 1, host.data(), host.size() * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  s->res_base = 0;
+  return e;
+}
+
+// Zero the flags and the status word (after a launch gave up, or a new initial state).
+cudaError_t resident_reset(lbm_sim* s) {
+  s->res_base = 0;
+  if (!s->res_mem) return cudaSuccess;
+  return cudaMemsetAsync(s->res_mem, 0, ((size_t)resident_tiles(s->nx, s->ny) + 1) * sizeof(unsigned int), s->stream);
+}
+
+cudaError_t launch_resident(lbm_sim* s, const Grid& g, int n) {
+  cudaError_t e = resident_prepare(s);
+  if (e != cudaSuccess) return e;
+  switch (g.storage) {
+    case ST_FP16: e = launch_resident_st<ST_FP16>(s, g, n); break;
+    case ST_BF16: e = launch_resident_st<ST_BF16>(s, g, n); break;
+    default: e = launch_resident_st<ST_FP32>(s, g, n); break;
+  }
+  if (e == cudaSuccess) {
+    s->res_base += (unsigned int)n;
+    s->res_used = true;
+  }
+  return e;
+}
 
 cudaError_t launch_tile2d(const Phys& P, const Grid& g, cudaStream_t st) {
   switch (g.storage) {

@@ -274,6 +274,62 @@ def test_tile_kernel_equals_row_march(lbm, nx, ny, bcx, bcy, rf, ch, fs, st, see
     assert np.array_equal(tiles.checkpoint(), rows.checkpoint())
 
 
+RESIDENT_CASES = TILE_CASES + [
+    # more tiles than one wave of resident CTAs: each CTA steps several tiles in turn
+    (300, 150, W.PERIODIC, W.WALL, 1, 0, 0, 0, 9),
+    (512, 512, W.PERIODIC, W.PERIODIC, 0, 0, 0, 0, 10),
+    (250, 300, W.WALL, W.WALL, 0, 1, 0, 1, 11),
+]
+
+
+@pytest.mark.parametrize("nx,ny,bcx,bcy,rf,ch,fs,st,seed", RESIDENT_CASES)
+def test_resident_kernel_equals_tile_kernel(lbm, nx, ny, bcx, bcy, rf, ch, fs, st, seed):
+    """The resident form (n steps in one launch, each tile waiting only on the tiles within its
+    reach) gives the tile kernel's state bitwise, over several calls of odd and even lengths (a
+    launch that starts from either buffer, the flags carried from one launch to the next)."""
+    import dataclasses
+    w = W.random_small(nx, ny, seed=seed, bc_x=bcx, bc_y=bcy, gravity=1e-5 if bcy == W.WALL else 0.0,
+                       remove_Fa=rf)
+    w = dataclasses.replace(w, phys=dataclasses.replace(w.phys, ch_conservative=ch, fs_form=fs))
+    tiles = lbm.Sim.from_workload(w, storage=st, kernel=lbm.LBM_KERNEL_TILES)
+    res = lbm.Sim.from_workload(w, storage=st, kernel=lbm.LBM_KERNEL_RESIDENT)
+    for n in (7, 1, 12, 20):
+        tiles.step(n)
+        before = res.launch_count
+        res.step(n)
+        assert res.launch_count - before == 1
+        assert res.step_status() == 0
+        assert np.array_equal(res.checkpoint(), tiles.checkpoint()), n
+
+
+def test_resident_wait_runs_out_and_recovers(lbm):
+    """A tile that never announces its step (the host's hold_tile hook) makes its neighbours'
+    bounded waits run out: the launch ends by itself well within a second, lbm_step_status and
+    lbm_diagnostics report LBM_ERR_TIMEOUT, later launches do nothing until the status is read,
+    and after a new initial state the resident kernel again matches the tile kernel bitwise."""
+    import time
+    w = W.static_droplet()
+    res = lbm.Sim.from_workload(w, kernel=lbm.LBM_KERNEL_RESIDENT)
+    res.set_wait_limit(20_000_000, hold_tile=37)         # 20 ms
+    t0 = time.perf_counter()
+    res.step(50)
+    assert res.step_status() == lbm._lib.LBM_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    assert res.step_status() == 0                        # read once, then re-armed
+    res.step(10)                                         # held again: gives up again
+    with pytest.raises(lbm.LBMError) as e:
+        res.diagnostics()
+    assert e.value.code == lbm._lib.LBM_ERR_TIMEOUT
+    res.set_wait_limit(1_000_000_000)                    # no tile held
+    res.init_fields(*[np.ascontiguousarray(a, np.float32) for a in (w.phi0, w.ux0, w.uy0, w.p0)])
+    tiles = lbm.Sim.from_workload(w, kernel=lbm.LBM_KERNEL_TILES)
+    res.step(30)
+    tiles.step(30)
+    assert res.step_status() == 0
+    assert np.array_equal(res.checkpoint(), tiles.checkpoint())
+    assert res.diagnostics()["finite"]
+
+
 def test_tile_kernel_refused_where_it_does_not_apply(lbm):
     import dataclasses
     w = W.random_small(40, 24, seed=3)
@@ -281,6 +337,8 @@ def test_tile_kernel_refused_where_it_does_not_apply(lbm):
     s = lbm.Sim.from_workload(w)
     with pytest.raises(lbm.LBMError):
         s.set_kernel(lbm.LBM_KERNEL_TILES)
+    with pytest.raises(lbm.LBMError):
+        s.set_kernel(lbm.LBM_KERNEL_RESIDENT)
 
 
 @pytest.mark.parametrize("rf", [0, 1])
