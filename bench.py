@@ -295,11 +295,25 @@ def serve_leg(args, lbm, torch):
 
 def other_grids(lbm, torch, peak):
     """Secondary lines: a 4096 x 4096 periodic static drop (2.4 GB ping-pong, far above L2) and the
-    L2-resident c1 / c2 grids, each with its autotuned tile, timed over consecutive steps (no
-    flush: the large grid does not fit in L2, the small ones are labelled L2-resident)."""
+    L2-resident c1 / c2 grids, each on the kernel the library picks by default, timed over
+    consecutive steps (no flush: the large grid does not fit in L2, the small ones are labelled
+    L2-resident).  The small grids run the tile kernel; for them the row march is timed too, on
+    its autotuned tile in the same run, and the ratio is reported."""
     import workloads as W
     from paper_1110_5004_gb300 import autotune
     stream = torch.cuda.current_stream()
+
+    def time_steps(sim, w, steps):
+        sim.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
+        sim.step(3)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        sim.step(steps)
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) * 1e-3 / steps
+
     out = {}
     for key, w, steps, label in (("large_grid", W.static_droplet(nx=4096, ny=4096, R=600.0), 20, "exceeds L2"),
                                  ("c1", W.static_droplet(), 400, "L2-resident"),
@@ -309,21 +323,20 @@ def other_grids(lbm, torch, peak):
         # which the row-march tile shape has no effect
         small = w.cells <= 1 << 19
         t_, r_ = (0, 0) if small else autotune.tune_sim(sim)[:2]
-        sim.init_fields(w.phi0, w.ux0, w.uy0, w.p0)
-        sim.step(3)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        sim.step(steps)
-        b.record(stream)
-        b.synchronize()
-        dt = a.elapsed_time(b) * 1e-3 / steps
+        dt = time_steps(sim, w, steps)
+        sim.close()
         mlups = w.cells / dt / 1e6
         out[key] = {"workload": w.name, "cells": w.cells, "mlups": mlups, "us_per_step": dt * 1e6,
                     "hbm_frac_of_measured": B_MIN_FP32 * mlups * 1e6 / (peak * 1e9),
                     "kernel": "tiles (16 x 8 cells per CTA)" if small else "rows",
                     "tile": None if small else [t_, r_], "note": label}
-        sim.close()
+        if small:
+            rows = lbm.Sim.from_workload(w, stream=stream, kernel=lbm.LBM_KERNEL_ROWS)
+            rt, rr = autotune.tune_sim(rows)[:2]
+            drow = time_steps(rows, w, steps)
+            rows.close()
+            out[key].update({"rows_us_per_step": drow * 1e6, "rows_tile": [rt, rr],
+                             "speedup_vs_rows": drow / dt})
     return out
 
 

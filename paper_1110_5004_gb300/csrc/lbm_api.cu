@@ -355,7 +355,7 @@ int lbm_step(lbm_sim* s, int n) {
   const bool tiles = uses_tile2d(s);
   for (int i = 0; i < n; ++i) {
     Grid g = make_grid(s, s->buf[s->cur], s->buf[s->cur ^ 1]);
-    cudaError_t e = tiles ? launch_tile2d(s->phys, g, s->stream) : launch_step(s->phys, g, s->nt, s->stream);
+    cudaError_t e = tiles ? launch_tile2d(s->phys, g, s->sms, s->stream) : launch_step(s->phys, g, s->nt, s->stream);
     if (e != cudaSuccess) return cuda_fail(e, "lbm_step launch");
     s->cur ^= 1;
     s->steps++;

@@ -350,7 +350,11 @@ struct CollideC {
   float wphiD[3];   // FF: w_c phi div(u)
 };
 
-template <int ST, int A, bool FF>
+// PART: COLLIDE_BOTH, or only the gbar (COLLIDE_G) or only the f (COLLIDE_F) populations, each
+// computed exactly as in the joint form (the small-grid kernel gives them to two threads).
+constexpr int COLLIDE_BOTH = 0, COLLIDE_F = 1, COLLIDE_G = 2;
+
+template <int ST, int A, bool FF, int PART = COLLIDE_BOTH>
 __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q], const float gb[Q], const Grid& g,
                                             CellB cell, float& fsum, float& ofeqsum) {
   constexpr int C = A == 0 ? 0 : (A <= 4 ? 1 : 2);
@@ -367,9 +371,11 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
     t2 = fsub(eproj<A>(k.Dx, k.Dy, k.Dp, k.Dm), k.uD);
   }
   const float gmw = fmul(w, poly);
-  const float S = fmad(gmw, t2, t1w);
-  st_pop<ST>(g.dst, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
-  if (A > 0) {
+  if (PART != COLLIDE_F) {
+    const float S = fmad(gmw, t2, t1w);
+    st_pop<ST>(g.dst, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
+  }
+  if (A > 0 && PART != COLLIDE_G) {
     float ofeq;
     if constexpr (FF) {
       const float Ga = fadd(w, gmw);                                        // Gamma_a
@@ -387,7 +393,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
 // Collision of both distributions at one cell and store of the post-collision populations.
 // f[] holds f_1..f_8 (index 0 unused), gb[] gbar_0..gbar_8; gpx12/gpy12 are 12 grad p.
 // phiD = phi div(u) (convective form) or 0: the f collision adds w_a phiD to direction a.
-template <int ST, bool FF>
+template <int ST, bool FF, int PART = COLLIDE_BOTH>
 __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float p, float gpx12, float gpy12,
                                               float phi_hi, float phi_lo, float phiD, const float f[Q],
                                               const float gb[Q], const Grid& g, CellB cell) {
@@ -438,20 +444,21 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
     k.wphiD[2] = fmul(1.0f / 36.0f, phiD);
   }
   float fsum = 0.0f, ofeqsum = 0.0f;
-  collide_dir<ST, 0, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 1, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 2, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 3, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 4, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 5, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 6, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 7, FF>(k, f, gb, g, cell, fsum, ofeqsum);
-  collide_dir<ST, 8, FF>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 0, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 1, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 2, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 3, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 4, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 5, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 6, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 7, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
+  collide_dir<ST, 8, FF, PART>(k, f, gb, g, cell, fsum, ofeqsum);
   // f_0 = phi - sum_{a>0} f_a and omega_f (f_0^eq - f_0) = omega_f sum_{a>0} f_a - sum omega_f f^eq_a;
   // the directions a > 0 carry w_a phiD of the source inside ofeqsum, so the rest gets
   // phiD - (5/9) phiD = w_0 phiD by adding phiD:
   // f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum (omega_f f^eq_a + w_a phiD)) + phiD].
   // Only small terms are rounded before the one error-free sum with the O(1) high word.
+  if (PART == COLLIDE_G) return;
   float hi, lo;
   if constexpr (FF) {
     // the forced form changes phi by theta_M lap mu (+ phiD) in the collision

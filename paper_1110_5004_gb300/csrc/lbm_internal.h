@@ -66,7 +66,8 @@ void tile_geometry(int nx, int ny, int nt, int seg_h, int slots, int* tile_w, in
 int tile_occupancy(int nt);
 // The small-grid step kernel (lbm_tile2d.cu): s_form 0 and f_form 0.
 bool tile2d_eligible(const lbm_params& p);
-cudaError_t launch_tile2d(const Phys& P, const Grid& g, cudaStream_t st);
+// 384-thread CTAs when the grid's tiles fit one wave of them on `sms` multiprocessors, else 256.
+cudaError_t launch_tile2d(const Phys& P, const Grid& g, int sms, cudaStream_t st);
 // Grids of at most this many cells run the small-grid kernel by default.
 constexpr long long SMALL_GRID_CELLS = 1 << 19;
 bool uses_tile2d(const lbm_sim* s);

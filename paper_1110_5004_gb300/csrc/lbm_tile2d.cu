@@ -8,6 +8,8 @@
 //   S1  mu on the tile plus 2                        (Eq. 1)
 //   S2  u, p on the tile plus 1                      (pull of gbar; Eq. 4, 5, 8)
 //   S3  collide and store the tile                   (grad p, phi div u, both BGK collisions)
+// S0 keeps the pulled f of the tile's own cells and S2 their pulled gbar for S3, which splits
+// each cell's collision between two threads (f and gbar).
 // Every per-cell operation is the shared stage function the row march uses (lbm_device.cuh), with
 // the same neighbour values: cells next to a wall also write their value into the mirrored ghost
 // position, as in the row march, so the state is bitwise the one the row march computes.
@@ -25,6 +27,7 @@ struct Smem2D {
   float hi[FH][FW], lo[FH][FW], mu[FH][FW], p[FH][FW], ux[FH][FW], uy[FH][FW];
   float rec[10][TY][TX];   // S2 -> S3 record of the tile's cells (Rec fields phi .. ogr3)
   float gb[Q][TY][TX];     // their pulled gbar populations
+  unsigned int f3[Q - 1][TY][TX];   // their pulled f_1..f_8 (stored bits), handed from S0 to S3
 };
 
 // One step of tile `tile` (row-major over tiles_x columns of tiles) from g.src into g.dst.  COH:
@@ -55,10 +58,13 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
     cn = make_col<ST>(wrap1(x, g.nx), g);
     rn = make_row(wrap1(y, g.ny), g);
   };
-  // Every population load of this thread is issued first, all at once: f of its S0 cells, gbar
-  // of its S2 cells and f of its S3 cell; the passes then wait on the loads they use.
-  constexpr int C0 = (FW * FH + NT - 1) / NT, C2 = ((FW - 4) * (FH - 4) + NT - 1) / NT, C3 = (TX * TY + NT - 1) / NT;
-  unsigned int f0raw[C0][NF], g2raw[C2][Q], f3raw[C3][Q];
+  // Every population load of this thread is issued first, all at once: f of its S0 cells and
+  // gbar of its S2 cells; the passes then wait on the loads they use.
+  constexpr int C0 = (FW * FH + NT - 1) / NT, C2 = ((FW - 4) * (FH - 4) + NT - 1) / NT;
+  // Two threads per tile cell in S3: a cell's f collision goes to thread k and its gbar collision
+  // to thread k + TX * TY, so the longest stage runs at half the chain.
+  static_assert(NT >= 2 * TX * TY, "S3 needs two threads per tile cell");
+  unsigned int f0raw[C0][NF], g2raw[C2][Q];
 #pragma unroll
   for (int c = 0; c < C0; ++c) {
     const int k = t + c * NT, i = k % FW, j = k / FW, x = x0 - 3 + i, y = y0 - 3 + j;
@@ -80,18 +86,8 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
       gather9<ST, Q, COH>(g.src, cn, rn, g2raw[c]);
     }
   }
-#pragma unroll
-  for (int c = 0; c < C3; ++c) {
-    const int k = t + c * NT, x = x0 + k % TX, y = y0 + k / TX;
-    if (k < TX * TY && x < g.nx && y < g.ny) {
-      ColNb cn;
-      RowNb rn;
-      nbr(x, y, cn, rn);
-      gather9<ST, 0, COH>(g.src, cn, rn, f3raw[c]);   // the collision's f populations
-    }
-  }
 
-  // ---- S0: phi on the frame
+  // ---- S0: phi on the frame; the pulled f_1..f_8 of the tile's own cells are kept for S3
 #pragma unroll
   for (int c = 0; c < C0; ++c) {
     const int k = t + c * NT, i = k % FW, j = k / FW, x = x0 - 3 + i, y = y0 - 3 + j;
@@ -104,6 +100,11 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
     phi_pair(fp, hi, lo);
     put(sm.hi, i, j, x, y, hi);
     put(sm.lo, i, j, x, y, lo);
+    const int ti = i - 3, tj = j - 3;
+    if (ti >= 0 && ti < TX && tj >= 0 && tj < TY) {
+#pragma unroll
+      for (int a = 1; a < Q; ++a) sm.f3[a - 1][tj][ti] = f0raw[c][a];
+    }
   }
   __syncthreads();
   // ---- S1: mu on the frame less one ring
@@ -147,34 +148,42 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
   }
   __syncthreads();
   // ---- S3: collide and store the tile's own cells
+  {
+    const int k = t % (TX * TY), ti = k % TX, tj = k / TX, i = ti + 3, j = tj + 3, x = x0 + ti, y = y0 + tj;
+    if (t < 2 * TX * TY && x < g.nx && y < g.ny) {
+      Rec r{};
+      r.phi = sm.rec[0][tj][ti];
+      r.mu = sm.rec[1][tj][ti];
+      r.ux = sm.rec[2][tj][ti];
+      r.uy = sm.rec[3][tj][ti];
+      r.Fx = sm.rec[4][tj][ti];
+      r.Fy = sm.rec[5][tj][ti];
+      r.mrx3 = sm.rec[6][tj][ti];
+      r.mry3 = sm.rec[7][tj][ti];
+      r.og = sm.rec[8][tj][ti];
+      r.ogr3 = sm.rec[9][tj][ti];
+      float f[Q], gb[Q];
+      const CellB cell = cell_at(y * g.row_bytes, col_bytes<ST>(x));
+      if (t < TX * TY) {   // f: needs phi div u and the phi pair, not p
+        const float phiD = P.ch_conv ? phi_div_u(r.phi, &sm.ux[j - 1][i], &sm.ux[j][i], &sm.ux[j + 1][i],
+                                                 &sm.uy[j - 1][i], &sm.uy[j + 1][i])
+                                     : 0.0f;
+        f[0] = 0.0f;   // unused: f_0 follows from the phi pair
 #pragma unroll
-  for (int c = 0; c < C3; ++c) {
-    const int k = t + c * NT, ti = k % TX, tj = k / TX, i = ti + 3, j = tj + 3, x = x0 + ti, y = y0 + tj;
-    if (k >= TX * TY || x >= g.nx || y >= g.ny) continue;
-    float gpx, gpy;
-    grad12(&sm.p[j - 1][i], &sm.p[j][i], &sm.p[j + 1][i], gpx, gpy);
-    Rec r{};
-    r.phi = sm.rec[0][tj][ti];
-    r.mu = sm.rec[1][tj][ti];
-    r.ux = sm.rec[2][tj][ti];
-    r.uy = sm.rec[3][tj][ti];
-    r.Fx = sm.rec[4][tj][ti];
-    r.Fy = sm.rec[5][tj][ti];
-    r.mrx3 = sm.rec[6][tj][ti];
-    r.mry3 = sm.rec[7][tj][ti];
-    r.og = sm.rec[8][tj][ti];
-    r.ogr3 = sm.rec[9][tj][ti];
-    const float phiD = P.ch_conv ? phi_div_u(r.phi, &sm.ux[j - 1][i], &sm.ux[j][i], &sm.ux[j + 1][i], &sm.uy[j - 1][i],
-                                             &sm.uy[j + 1][i])
-                                 : 0.0f;
-    float f[Q], gb[Q];
-    f[0] = 0.0f;                          // unused: f_0 follows from the phi pair
+        for (int a = 1; a < Q; ++a) f[a] = dec_pop<ST>(sm.f3[a - 1][tj][ti], a, g.isf);
 #pragma unroll
-    for (int a = 1; a < Q; ++a) f[a] = dec_pop<ST>(f3raw[c][a], a, g.isf);
+        for (int a = 0; a < Q; ++a) gb[a] = 0.0f;   // unused by the f collision
+        collide_store<ST, false, COLLIDE_F>(P, r, 0.0f, 0.0f, 0.0f, sm.hi[j][i], sm.lo[j][i], phiD, f, gb, g, cell);
+      } else {              // gbar: needs p and grad p
+        float gpx, gpy;
+        grad12(&sm.p[j - 1][i], &sm.p[j][i], &sm.p[j + 1][i], gpx, gpy);
 #pragma unroll
-    for (int a = 0; a < Q; ++a) gb[a] = sm.gb[a][tj][ti];
-    collide_store<ST, false>(P, r, sm.p[j][i], gpx, gpy, sm.hi[j][i], sm.lo[j][i], phiD, f, gb, g,
-                             cell_at(y * g.row_bytes, col_bytes<ST>(x)));
+        for (int a = 0; a < Q; ++a) f[a] = 0.0f;    // unused by the gbar collision
+#pragma unroll
+        for (int a = 0; a < Q; ++a) gb[a] = sm.gb[a][tj][ti];
+        collide_store<ST, false, COLLIDE_G>(P, r, sm.p[j][i], gpx, gpy, 0.0f, 0.0f, 0.0f, f, gb, g, cell);
+      }
+    }
   }
 }
 
@@ -212,15 +221,27 @@ static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_
   return cudaLaunchKernelEx(&cfg, k_tile2d<ST, TX, TY, NT>, P, g, tx);
 }
 
-// 16 x 8 cells per CTA of 256 threads: every frame cell of S0 in two rounds, one for S1 and S2.
-// Measured against 16 x 8 / 128 and 384 threads, 16 x 4 / 256, 8 x 8 / 64, 128 and 256,
-// 16 x 16 / 256, 32 x 4 / 256 and 32 x 8 / 256 on 128^2, 300 x 150, 150 x 450, 256 x 1024 and
-// 512^2 grids: fastest or within 3 % on each but 300 x 150, where 16 x 8 / 384 is 11 % faster and
-// every other grid 1-20 % slower.
-constexpr int T2D_TX = 16, T2D_TY = 8, T2D_NT = 256;
+// 16 x 8 cells per CTA.  256 threads: every frame cell of S0 in two rounds, one for S1 and S2,
+// and the collisions split between the f and gbar threads.  Measured against 16 x 8 / 128
+// threads, 16 x 4 / 256, 8 x 8 / 64, 128 and 256, 16 x 16 / 256, 32 x 4 / 256 and 32 x 8 / 256
+// on 128^2, 300 x 150, 150 x 450, 256 x 1024 and 512^2 grids: fastest or within 3 % on each.
+// 384 threads (S0 in one round; 3 CTAs per SM) is 10-12 % faster on grids whose tiles fit one
+// wave of it (128^2, 300 x 150) and 9-18 % slower on the others, so it runs where the tiles fit
+// one wave; 512 threads was slower than 384 on every grid.
+constexpr int T2D_TX = 16, T2D_TY = 8, T2D_NT = 256, T2D_NT_WAVE = 384;
 
 template <int ST>
-static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, cudaStream_t st) {
+static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, int sms, cudaStream_t st) {
+  static int slots = -1;   // CTAs of the 384-thread form resident at once (one GPU per process)
+  if (slots < 0) {
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, k_tile2d<ST, T2D_TX, T2D_TY, T2D_NT_WAVE>, T2D_NT_WAVE, sizeof(Smem2D<T2D_TX, T2D_TY>));
+    if (e != cudaSuccess) return e;
+    slots = occ * sms;
+  }
+  const long long tiles = (long long)((g.nx + T2D_TX - 1) / T2D_TX) * ((g.ny + T2D_TY - 1) / T2D_TY);
+  if (tiles <= slots) return launch_tile2d_shape<ST, T2D_TX, T2D_TY, T2D_NT_WAVE>(P, g, st);
   return launch_tile2d_shape<ST, T2D_TX, T2D_TY, T2D_NT>(P, g, st);
 }
 
@@ -438,11 +459,11 @@ cudaError_t launch_resident(lbm_sim* s, const Grid& g, int n) {
   return e;
 }
 
-cudaError_t launch_tile2d(const Phys& P, const Grid& g, cudaStream_t st) {
+cudaError_t launch_tile2d(const Phys& P, const Grid& g, int sms, cudaStream_t st) {
   switch (g.storage) {
-    case ST_FP16: return launch_tile2d_st<ST_FP16>(P, g, st);
-    case ST_BF16: return launch_tile2d_st<ST_BF16>(P, g, st);
-    default: return launch_tile2d_st<ST_FP32>(P, g, st);
+    case ST_FP16: return launch_tile2d_st<ST_FP16>(P, g, sms, st);
+    case ST_BF16: return launch_tile2d_st<ST_BF16>(P, g, sms, st);
+    default: return launch_tile2d_st<ST_FP32>(P, g, sms, st);
   }
 }
 

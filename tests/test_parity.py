@@ -255,6 +255,9 @@ TILE_CASES = [
     (47, 38, W.WALL, W.WALL, 1, 0, 0, 1, 6),
     (40, 24, W.PERIODIC, W.WALL, 0, 0, 0, 2, 7),
     (150, 90, W.PERIODIC, W.WALL, 1, 0, 0, 0, 8),
+    # more tiles than one wave of the 384-thread form: the 256-thread form runs
+    (400, 200, W.WALL, W.PERIODIC, 1, 1, 0, 0, 12),
+    (400, 200, W.PERIODIC, W.WALL, 0, 0, 1, 1, 13),
 ]
 
 
