@@ -581,7 +581,9 @@ __device__ __forceinline__ float phi_div_u(float phi, const float* xs, const flo
 // Inlined into both kernels; its arithmetic is fixed by the explicit intrinsics above.
 // SD: the direct mass defect (s_form 1) is compiled in; kernels without it carry none of its code.
 // FF: the forced order-parameter LBE (f_form 1; FP32 storage only).
-template <int NT, int MODE, int ST, bool SD, bool FF = false>
+// XW: the x axis may have walls; false (a periodic x axis) compiles out the ghost columns and the
+// column wall tests of the gathers.
+template <int NT, int MODE, int ST, bool SD, bool FF = false, bool XW = true>
 __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
                                       Smem<NT>& sm) {
   const int t = threadIdx.x;
@@ -591,7 +593,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   const int ya = seg * g.seg_h;
   const int yb = min(ya + g.seg_h, g.ny);
   const int xl = x0 - 3 + t;                 // logical column (may lie outside [0, nx))
-  const bool xwall = g.bc_x == BC_WALL;
+  const bool xwall = XW && g.bc_x == BC_WALL;
   const bool ywall = g.bc_y == BC_WALL;
   const bool col_real = !xwall || (xl >= 0 && xl < g.nx);
   const int xp = wrap1(xl, g.nx);
@@ -612,7 +614,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto ghost_slot = [&](int r) { return r == 0 ? slot(-1) : slot(g.ny); };
   auto is_wall_row = [&](int r) { return ywall && (r == 0 || r == g.ny - 1); };
   auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
-  const ColNb cn = make_col<ST>(xp, g);
+  ColNb cn = make_col<ST>(xp, g);
+  if constexpr (!XW) cn.wl = cn.wr = false;
   constexpr int USLOT = 2 * NT;
   float* const uring = &sm.urows[0][0][0];
   // Ring slot of row r; the ghost rows beyond a wall (-1, ny) have slots of their own, since a
@@ -629,12 +632,12 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   // store field F of row r (slot offset so) plus its mirrored ghost copies
   auto put = [&](int so, int r, int F, float v, auto checked) {
     ring[so + F * NT + t] = v;
-    ring[so + F * NT + tgi] = v;             // a second store to the own column when no ghost
+    if constexpr (XW) ring[so + F * NT + tgi] = v;   // a second store to the own column when no ghost
     if constexpr (decltype(checked)::value) {
       if (is_wall_row(r)) {
         const int gs = ghost_slot(r);
         ring[gs + F * NT + t] = v;
-        ring[gs + F * NT + tgi] = v;
+        if constexpr (XW) ring[gs + F * NT + tgi] = v;
       }
     }
   };
@@ -643,16 +646,20 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto put_u = [&](int r, float ux, float uy, auto checked) {
     const int so = uslot(r);
     uring[so + t] = ux;
-    uring[so + tgi] = ux;
     uring[so + NT + t] = uy;
-    uring[so + NT + tgi] = uy;
+    if constexpr (XW) {
+      uring[so + tgi] = ux;
+      uring[so + NT + tgi] = uy;
+    }
     if constexpr (decltype(checked)::value) {
       if (is_wall_row(r)) {
         const int gs = r == 0 ? RING_U * USLOT : (RING_U + 1) * USLOT;
         uring[gs + t] = ux;
-        uring[gs + tgi] = ux;
         uring[gs + NT + t] = uy;
-        uring[gs + NT + tgi] = uy;
+        if constexpr (XW) {
+          uring[gs + tgi] = ux;
+          uring[gs + NT + tgi] = uy;
+        }
       }
     }
   };
