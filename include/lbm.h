@@ -52,8 +52,8 @@ extern "C" {
 #define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math */
 
 /* step kernel (lbm_set_kernel) */
-#define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel on grids of at most 524288 cells where it applies,
-                              else the row march */
+#define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel where it applies on grids of at most 196608 cells
+                              (262144 with walls on x), else the row march */
 #define LBM_KERNEL_ROWS 1  /* strips marching rows: every configuration */
 #define LBM_KERNEL_TILES 2 /* 2-D tiles in four shared-memory passes: s_form 0, f_form 0 */
 #define LBM_KERNEL_RESIDENT 3 /* the 2-D tiles kept resident: one launch per lbm_step call */
@@ -254,6 +254,10 @@ LBM_API int lbm_set_kernel(lbm_sim* sim, int kernel);
  *   gave up since the status was last read, else LBM_OK.
  * Errors: LBM_ERR_INVALID_ARG for a NULL sim or timeout_ns <= 0; LBM_ERR_CUDA. */
 LBM_API int lbm_set_wait_limit(lbm_sim* sim, long long timeout_ns, int hold_tile);
+/* The kernel lbm_step runs for this simulation under its current choice: LBM_KERNEL_ROWS,
+ * LBM_KERNEL_TILES or LBM_KERNEL_RESIDENT (AUTO resolved; a resident choice runs the tile kernel
+ * for single steps); LBM_ERR_INVALID_ARG for a NULL sim. */
+LBM_API int lbm_active_kernel(const lbm_sim* sim);
 LBM_API int lbm_step_status(lbm_sim* sim);
 
 /* Kernel launches issued by this simulation since creation (step, init, moments,

@@ -126,6 +126,11 @@ class Sim:
         (bitwise the same results; the tile kernels need s_form 0 and f_form 0)."""
         _lib.check(lib().lbm_set_kernel(self._h, int(kernel)))
 
+    @property
+    def active_kernel(self):
+        """lbm_active_kernel: the LBM_KERNEL_* value lbm_step runs (AUTO resolved)."""
+        return _lib.check_value(lib().lbm_active_kernel(self._h))
+
     def set_wait_limit(self, timeout_ns, hold_tile=-1):
         """lbm_set_wait_limit: bound of the resident kernel's waits; hold_tile >= 0 makes that
         tile never announce a finished step (the test of the bound)."""

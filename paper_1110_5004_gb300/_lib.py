@@ -26,7 +26,7 @@ EXPORTS = (
     "lbm_batch_add", "lbm_batch_remove", "lbm_batch_step", "lbm_batch_size", "lbm_batch_bytes",
     "lbm_batch_destroy", "lbm_diagnostics_fields_noalloc", "lbm_batch_set_tile", "lbm_checkpoint_bytes",
     "lbm_checkpoint", "lbm_restore", "lbm_sim_device_bytes", "lbm_init_fields_packed", "lbm_moments_packed",
-    "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_status",
+    "lbm_set_kernel", "lbm_set_wait_limit", "lbm_step_status", "lbm_active_kernel",
 )
 
 
@@ -87,6 +87,7 @@ def load(path: str = LIB_PATH):
         "lbm_set_kernel": (ip, [vp, ip]),
         "lbm_set_wait_limit": (ip, [vp, ctypes.c_longlong, ip]),
         "lbm_step_status": (ip, [vp]),
+        "lbm_active_kernel": (ip, [vp]),
         "lbm_launch_count": (ctypes.c_longlong, [vp]),
         "lbm_strerror": (ctypes.c_char_p, [ip]),
         "lbm_last_error": (ctypes.c_char_p, []),
@@ -118,5 +119,12 @@ def _strerror(code):
 
 def check(rc):
     if rc != LBM_OK:
+        raise LBMError(rc, load().lbm_last_error().decode())
+    return rc
+
+
+def check_value(rc):
+    """For calls that return a non-negative value or a negative LBM_ERR_* code."""
+    if rc < 0:
         raise LBMError(rc, load().lbm_last_error().decode())
     return rc

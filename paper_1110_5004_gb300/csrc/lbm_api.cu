@@ -101,8 +101,8 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
 
 bool uses_tile2d(const lbm_sim* s) {
   if (s->kernel == LBM_KERNEL_ROWS || !tile2d_eligible(s->params)) return false;
-  return s->kernel == LBM_KERNEL_TILES || s->kernel == LBM_KERNEL_RESIDENT ||
-         (long long)s->nx * s->ny <= SMALL_GRID_CELLS;
+  const long long limit = s->params.bc_x == LBM_WALL ? SMALL_GRID_CELLS_XWALL : SMALL_GRID_CELLS;
+  return s->kernel == LBM_KERNEL_TILES || s->kernel == LBM_KERNEL_RESIDENT || (long long)s->nx * s->ny <= limit;
 }
 
 static int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
@@ -609,6 +609,12 @@ int lbm_set_wait_limit(lbm_sim* s, long long timeout_ns, int hold_tile) {
 int lbm_step_status(lbm_sim* s) {
   if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
   return read_resident_status(s, true);
+}
+
+int lbm_active_kernel(const lbm_sim* s) {
+  if (!s) return set_error("sim is NULL"), LBM_ERR_INVALID_ARG;
+  if (s->kernel == LBM_KERNEL_RESIDENT) return LBM_KERNEL_RESIDENT;
+  return uses_tile2d(s) ? LBM_KERNEL_TILES : LBM_KERNEL_ROWS;
 }
 
 long long lbm_launch_count(const lbm_sim* s) { return s ? s->launches : -1; }
