@@ -52,8 +52,8 @@ extern "C" {
 #define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math */
 
 /* step kernel (lbm_set_kernel) */
-#define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel where it applies on grids of at most 196608 cells
-                              (262144 with walls on x), else the row march */
+#define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel where it applies on grids of at most 262144
+                              cells, else the row march */
 #define LBM_KERNEL_ROWS 1  /* strips marching rows: every configuration */
 #define LBM_KERNEL_TILES 2 /* 2-D tiles in four shared-memory passes: s_form 0, f_form 0 */
 #define LBM_KERNEL_RESIDENT 3 /* the 2-D tiles kept resident: one launch per lbm_step call */

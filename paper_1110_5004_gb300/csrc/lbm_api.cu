@@ -101,8 +101,8 @@ Grid make_grid(const lbm_sim* s, const void* src, void* dst) {
 
 bool uses_tile2d(const lbm_sim* s) {
   if (s->kernel == LBM_KERNEL_ROWS || !tile2d_eligible(s->params)) return false;
-  const long long limit = s->params.bc_x == LBM_WALL ? SMALL_GRID_CELLS_XWALL : SMALL_GRID_CELLS;
-  return s->kernel == LBM_KERNEL_TILES || s->kernel == LBM_KERNEL_RESIDENT || (long long)s->nx * s->ny <= limit;
+  return s->kernel == LBM_KERNEL_TILES || s->kernel == LBM_KERNEL_RESIDENT ||
+         (long long)s->nx * s->ny <= SMALL_GRID_CELLS;
 }
 
 static int pitch_of(int nx) { return (nx + 31) / 32 * 32; }

@@ -68,10 +68,9 @@ int tile_occupancy(int nt);
 bool tile2d_eligible(const lbm_params& p);
 // 384-thread CTAs when the grid's tiles fit one wave of them on `sms` multiprocessors, else 256.
 cudaError_t launch_tile2d(const Phys& P, const Grid& g, int sms, cudaStream_t st);
-// Grids of at most this many cells run the small-grid kernel by default: the row march's
-// periodic-x form catches up with it near 2^18 cells, its general form (x walls) later.
-constexpr long long SMALL_GRID_CELLS = 3 << 16;        // periodic x axis
-constexpr long long SMALL_GRID_CELLS_XWALL = 1 << 18;  // walls on x
+// Grids of at most this many cells run the small-grid kernel by default (measured faster up to
+// 2^18 cells, slower from 2^19 on, with and without x walls).
+constexpr long long SMALL_GRID_CELLS = 1 << 18;
 bool uses_tile2d(const lbm_sim* s);
 // The resident form: one launch of n >= 2 steps (flags and reach table prepared on first use).
 int resident_tiles(int nx, int ny);

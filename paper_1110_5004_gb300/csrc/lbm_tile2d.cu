@@ -32,13 +32,15 @@ struct Smem2D {
 
 // One step of tile `tile` (row-major over tiles_x columns of tiles) from g.src into g.dst.  COH:
 // population loads through L2 only, for a launch in which other CTAs write the state it reads.
-template <int ST, int TX, int TY, int NT, bool COH>
+// XW, YW: walls possible on x, on y; false (a periodic axis) compiles out that axis's wall tests
+// and ghost writes.
+template <int ST, int TX, int TY, int NT, bool COH, bool XW = true, bool YW = true>
 __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int tiles_x, int tile, Smem2D<TX, TY>& sm) {
   using S = Smem2D<TX, TY>;
   constexpr int FW = S::FW, FH = S::FH;
   const int t = threadIdx.x;
   const int x0 = (tile % tiles_x) * TX, y0 = (tile / tiles_x) * TY;
-  const bool xwall = g.bc_x == BC_WALL, ywall = g.bc_y == BC_WALL;
+  const bool xwall = XW && g.bc_x == BC_WALL, ywall = YW && g.bc_y == BC_WALL;
 
   // frame position (i, j) <-> logical cell (x0 - 3 + i, y0 - 3 + j)
   auto real = [&](int x, int y) {
@@ -57,6 +59,8 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
   auto nbr = [&](int x, int y, ColNb& cn, RowNb& rn) {
     cn = make_col<ST>(wrap1(x, g.nx), g);
     rn = make_row(wrap1(y, g.ny), g);
+    if constexpr (!XW) cn.wl = cn.wr = false;
+    if constexpr (!YW) rn.wb = rn.wt = false;
   };
   // Every population load of this thread is issued first, all at once: f of its S0 cells and
   // gbar of its S2 cells; the passes then wait on the loads they use.
@@ -187,7 +191,7 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
   }
 }
 
-template <int ST, int TX, int TY, int NT>
+template <int ST, int TX, int TY, int NT, bool XW, bool YW>
 __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // Launched as a programmatic dependent of the previous step: wait until that grid has
@@ -195,30 +199,66 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
   // its launch overlaps this one instead of following it.
   asm volatile("griddepcontrol.wait;" ::: "memory");
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-  tile2d_step<ST, TX, TY, NT, false>(P, g, tiles_x, blockIdx.x, *reinterpret_cast<Smem2D<TX, TY>*>(smem_raw));
+  tile2d_step<ST, TX, TY, NT, false, XW, YW>(P, g, tiles_x, blockIdx.x, *reinterpret_cast<Smem2D<TX, TY>*>(smem_raw));
 }
 
-template <int ST, int TX, int TY, int NT>
-static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_t st) {
+// Shared memory to ask for so that at most `cap` CTAs fit on an SM (at least `need`): a grid of
+// few tiles then spreads evenly over the SMs instead of piling several CTAs onto some while
+// others idle.  0 when the device attributes cannot be read.
+static int smem_for_cap(int need, int cap) {
+  static int per_sm = -1, reserved = 0, optin = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+      cudaGetLastError();
+      per_sm = 0;
+    }
+  }
+  if (per_sm <= 0) return need;
+  const int want = (per_sm / (cap + 1) - reserved + 16 + 15) / 16 * 16;   // cap + 1 no longer fit
+  if (want <= need || want > optin || cap * (want + reserved) > per_sm) return need;
+  return want;
+}
+
+template <int ST, int TX, int TY, int NT, bool XW, bool YW>
+static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, int sms, cudaStream_t st) {
   using S = Smem2D<TX, TY>;
   static bool attr_set = false;   // one GPU per process
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile2d<ST, TX, TY, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(S));
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tile2d<ST, TX, TY, NT, XW, YW>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int tx = (g.nx + TX - 1) / TX, ty = (g.ny + TY - 1) / TY;
+  const int tiles = tx * ty, cap = (tiles + sms - 1) / sms;   // CTAs per SM for one even wave
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(tx * ty);
+  cfg.gridDim = dim3(tiles);
   cfg.blockDim = dim3(NT);
-  cfg.dynamicSmemBytes = sizeof(S);
+  cfg.dynamicSmemBytes = smem_for_cap((int)sizeof(S), cap);
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_tile2d<ST, TX, TY, NT>, P, g, tx);
+  return cudaLaunchKernelEx(&cfg, k_tile2d<ST, TX, TY, NT, XW, YW>, P, g, tx);
+}
+
+constexpr int T2D_TX = 16, T2D_TY = 8, T2D_NT = 256, T2D_NT_WAVE = 384;
+
+// The wall forms: both axes periodic, walls on y only (the paper's experiments), or general.
+template <int ST, int NT>
+static cudaError_t launch_tile2d_bc(const Phys& P, const Grid& g, int sms, cudaStream_t st) {
+  if (g.bc_x != BC_WALL && g.bc_y != BC_WALL) return launch_tile2d_shape<ST, T2D_TX, T2D_TY, NT, false, false>(P, g, sms, st);
+  if (g.bc_x != BC_WALL) return launch_tile2d_shape<ST, T2D_TX, T2D_TY, NT, false, true>(P, g, sms, st);
+  return launch_tile2d_shape<ST, T2D_TX, T2D_TY, NT, true, true>(P, g, sms, st);
 }
 
 // 16 x 8 cells per CTA.  256 threads: every frame cell of S0 in two rounds, one for S1 and S2,
@@ -227,8 +267,8 @@ static cudaError_t launch_tile2d_shape(const Phys& P, const Grid& g, cudaStream_
 // on 128^2, 300 x 150, 150 x 450, 256 x 1024 and 512^2 grids: fastest or within 3 % on each.
 // 384 threads (S0 in one round; 3 CTAs per SM) is 10-12 % faster on grids whose tiles fit one
 // wave of it (128^2, 300 x 150) and 9-18 % slower on the others, so it runs where the tiles fit
-// one wave; 512 threads was slower than 384 on every grid.
-constexpr int T2D_TX = 16, T2D_TY = 8, T2D_NT = 256, T2D_NT_WAVE = 384;
+// one wave; 512 threads was slower than 384 on every grid.  Either way at most ceil(tiles / SMs)
+// CTAs share an SM (smem_for_cap).
 
 template <int ST>
 static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, int sms, cudaStream_t st) {
@@ -236,13 +276,13 @@ static cudaError_t launch_tile2d_st(const Phys& P, const Grid& g, int sms, cudaS
   if (slots < 0) {
     int occ = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, k_tile2d<ST, T2D_TX, T2D_TY, T2D_NT_WAVE>, T2D_NT_WAVE, sizeof(Smem2D<T2D_TX, T2D_TY>));
+        &occ, k_tile2d<ST, T2D_TX, T2D_TY, T2D_NT_WAVE, true, true>, T2D_NT_WAVE, sizeof(Smem2D<T2D_TX, T2D_TY>));
     if (e != cudaSuccess) return e;
     slots = occ * sms;
   }
   const long long tiles = (long long)((g.nx + T2D_TX - 1) / T2D_TX) * ((g.ny + T2D_TY - 1) / T2D_TY);
-  if (tiles <= slots) return launch_tile2d_shape<ST, T2D_TX, T2D_TY, T2D_NT_WAVE>(P, g, st);
-  return launch_tile2d_shape<ST, T2D_TX, T2D_TY, T2D_NT>(P, g, st);
+  if (tiles <= slots) return launch_tile2d_bc<ST, T2D_NT_WAVE>(P, g, sms, st);
+  return launch_tile2d_bc<ST, T2D_NT>(P, g, sms, st);
 }
 
 // ---- Resident form: one launch advances n steps.  Every CTA stays on the device and steps its

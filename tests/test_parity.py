@@ -334,17 +334,17 @@ def test_resident_wait_runs_out_and_recovers(lbm):
 
 
 def test_active_kernel_follows_the_measured_crossover(lbm):
-    """AUTO runs the tile kernel on grids of up to 196608 cells with a periodic x axis and up to
-    262144 with x walls (where each was measured faster), the row march above, and the row march
-    wherever the tile kernel does not apply; an explicit choice is reported as made."""
+    """AUTO runs the tile kernel on grids of up to 262144 cells (where it was measured faster,
+    with and without x walls), the row march above, and the row march wherever the tile kernel
+    does not apply; an explicit choice is reported as made."""
     import dataclasses
     xwall = lambda w: dataclasses.replace(w, phys=dataclasses.replace(w.phys, bc_x=W.WALL))
     cases = [(W.static_droplet(), lbm.LBM_KERNEL_TILES),
-             (W.static_droplet(nx=384, ny=512, R=80), lbm.LBM_KERNEL_TILES),     # 196608 cells
-             (W.static_droplet(nx=512, ny=512, R=100), lbm.LBM_KERNEL_ROWS),
+             (W.static_droplet(nx=512, ny=512, R=100), lbm.LBM_KERNEL_TILES),    # 262144 cells
+             (W.falling_droplet(), lbm.LBM_KERNEL_TILES),
              (xwall(W.static_droplet(nx=512, ny=512, R=100)), lbm.LBM_KERNEL_TILES),
-             (xwall(W.static_droplet(nx=1024, ny=512, R=100)), lbm.LBM_KERNEL_ROWS),
-             (W.falling_droplet(), lbm.LBM_KERNEL_ROWS)]
+             (W.static_droplet(nx=513, ny=512, R=100), lbm.LBM_KERNEL_ROWS),
+             (xwall(W.static_droplet(nx=1024, ny=512, R=100)), lbm.LBM_KERNEL_ROWS)]
     for w, want in cases:
         s = lbm.Sim.from_workload(w, init=False)
         assert s.active_kernel == want, (w.nx, w.ny)
