@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--tile", default="", help="threads,rows of the step kernel (default: autotuned)")
     ap.add_argument("--e2e-iters", type=int, default=20)
+    ap.add_argument("--e2e-jobs", type=int, default=4, help="simulations (streams) in flight in the e2e leg")
     ap.add_argument("--cpu-steps", type=int, default=480,
                     help="oracle steps for the CPU baseline sample on the splash (~10 s); scaled by cells")
     ap.add_argument("--no-cpu", action="store_true")
@@ -507,13 +508,14 @@ def run_ours(args):
         sim.step(REINIT_EVERY)
         sim.moments(h_out_np)
 
-    # the same work as two jobs in flight: two simulations on two streams, each driven by its own
-    # host thread through the packed calls (one upload and one download per iteration), so that
-    # one job's host copies overlap the other's steps
+    # the same work as several jobs in flight (--e2e-jobs): one simulation per stream, each driven
+    # by its own host thread through the packed calls (one upload and one download per
+    # iteration), so that one job's host copies overlap the others' steps
+    jobs = max(1, args.e2e_jobs)
     h_block = torch.from_numpy(np.stack([getattr(w, k) for k in ("phi0", "ux0", "uy0", "p0")])).pin_memory().numpy()
-    h_res = [torch.empty((5, w.ny, w.nx), dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
-    side = torch.cuda.Stream()
-    sims2 = [sim, lbm.Sim.from_workload(w, stream=side, tile=tile, storage=storage)]
+    h_res = [torch.empty((5, w.ny, w.nx), dtype=torch.float32).pin_memory().numpy() for _ in range(jobs)]
+    sims2 = [sim] + [lbm.Sim.from_workload(w, stream=torch.cuda.Stream(), tile=tile, storage=storage)
+                     for _ in range(jobs - 1)]
 
     def e2e_job(j, iters):
         s = sims2[j]
@@ -523,7 +525,8 @@ def run_ours(args):
             s.moments_packed(h_res[j])
 
     def e2e_pipelined(iters):
-        th = [threading.Thread(target=e2e_job, args=(j, n)) for j, n in enumerate((iters - iters // 2, iters // 2))]
+        share = [iters // jobs + (1 if j < iters % jobs else 0) for j in range(jobs)]
+        th = [threading.Thread(target=e2e_job, args=(j, n)) for j, n in enumerate(share)]
         for t_ in th:
             t_.start()
         for t_ in th:
@@ -583,9 +586,9 @@ def run_ours(args):
                         "h2d_bytes_per_step": 4 * 4 * w.cells // REINIT_EVERY,
                         "d2h_bytes_per_step": 5 * 4 * w.cells // REINIT_EVERY,
                         "what": "per iteration: lbm_init_fields_packed from a pinned host block (4 fields), "
-                                "lbm_step(%d), lbm_moments_packed into a pinned host block (5 fields); two "
-                                "simulations on two streams, each driven by its own host thread; bytes shown "
-                                "per LBM step" % REINIT_EVERY,
+                                "lbm_step(%d), lbm_moments_packed into a pinned host block (5 fields); %d "
+                                "simulations on %d streams, each driven by its own host thread; bytes shown "
+                                "per LBM step" % (REINIT_EVERY, jobs, jobs),
                         "serial_value": e2e_serial,
                         "serial_what": "one simulation, per-field lbm_init_fields / lbm_moments, iterations "
                                        "back to back"},
