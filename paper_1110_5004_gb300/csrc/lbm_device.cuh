@@ -612,8 +612,11 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   auto slot = [&](int r) { return (r * SLOT) & RMASK; };
   // ghost row beyond a wall filled together with real row r (its mirror), as a slot offset
   auto ghost_slot = [&](int r) { return r == 0 ? slot(-1) : slot(g.ny); };
-  auto is_wall_row = [&](int r) { return ywall && (r == 0 || r == g.ny - 1); };
-  auto row_ok = [&](int r) { return !ywall || (r >= 0 && r < g.ny); };
+  // A segment whose touched rows (ya - 9 .. yb + 6, over its whole march) are all interior
+  // needs none of the wrap and wall handling in its checked iterations, only the stage tests.
+  const bool seg_interior = ya >= 9 && yb + 6 <= g.ny - 1;
+  auto is_wall_row = [&](int r) { return !seg_interior && ywall && (r == 0 || r == g.ny - 1); };
+  auto row_ok = [&](int r) { return seg_interior || !ywall || (r >= 0 && r < g.ny); };
   ColNb cn = make_col<ST>(xp, g);
   if constexpr (!XW) cn.wl = cn.wr = false;
   constexpr int USLOT = 2 * NT;
@@ -622,6 +625,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   // 4-row ring would put the top one on a row that S3 of the previous iteration still reads.
   auto uslot = [&](int r) { return (r & (RING_U - 1)) * USLOT; };
   auto uslot_ck = [&](int r) {
+    if (seg_interior) return uslot(r);
     return ywall && r < 0 ? RING_U * USLOT : (ywall && r >= g.ny ? (RING_U + 1) * USLOT : uslot(r));
   };
 
@@ -668,19 +672,18 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   unsigned int fpr[NF], gpr[Q];
   unsigned int spr[2];                       // direct mass defect: rho, div(rho u) of the last step
   auto row_nb = [&](int r, auto checked) {
+    RowNb rn;
     if constexpr (decltype(checked)::value) {
-      return make_row(wrap1(r, g.ny), g);
-    } else {
-      RowNb rn;
-      rn.r0 = r * g.pitch;
-      rn.rm = rn.r0 - g.pitch;
-      rn.rq = rn.r0 + g.pitch;
-      rn.b0 = r * g.row_bytes;
-      rn.bm = rn.b0 - g.row_bytes;
-      rn.bq = rn.b0 + g.row_bytes;
-      rn.wb = rn.wt = false;
-      return rn;
+      if (!seg_interior) return make_row(wrap1(r, g.ny), g);
     }
+    rn.r0 = r * g.pitch;
+    rn.rm = rn.r0 - g.pitch;
+    rn.rq = rn.r0 + g.pitch;
+    rn.b0 = r * g.row_bytes;
+    rn.bm = rn.b0 - g.row_bytes;
+    rn.bq = rn.b0 + g.row_bytes;
+    rn.wb = rn.wt = false;
+    return rn;
   };
   auto fetch_f = [&](int r, auto checked) {
     const RowNb rn = row_nb(r, checked);
@@ -755,7 +758,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         grad12(hs, h0, hn, gphx, gphy);
         grad12(ms, m0, mn, gmx, gmy);
         // cell index of row r for the direct mass defect's planes (periodic halo rows wrap)
-        auto cell_of = [&]() { return (IN ? r : wrap1(r, g.ny)) * g.pitch + xp; };
+        auto cell_of = [&]() { return (IN || seg_interior ? r : wrap1(r, g.ny)) * g.pitch + xp; };
         float sdef = 0.0f;
         if (P.remove_Fa || (MODE == MODE_MOMENTS && mo.fax)) {
           if constexpr (SD) {
