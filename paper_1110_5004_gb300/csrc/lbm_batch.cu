@@ -41,9 +41,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
     g.dst = odd ? const_cast<void*>(d.buf0) : d.buf1;
     // members may differ in storage; the branch is uniform per tile
     switch (g.storage) {
-      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      default: run_tile<NT, MODE_STEP, ST_FP32, SD>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      default: run_tile<NT, MODE_STEP, ST_FP32, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
     }
     __syncthreads();  // shared rings are reused by the next tile
   }

@@ -322,7 +322,7 @@ struct Smem {
   float rows[RING][R_FIELDS][NT];  // phi (hi, lo), mu, p of recent rows
   float urows[RING_U + 2][2][NT];  // u_x, u_y of recent rows (convective form only)
   float2 f[RING_F][NT][NFR / 2];   // own column only (no barrier needed); 64-bit accesses
-  float g[2][Q][NT];               // own column only
+  float g[2][Q][NT];               // own column only; the S2 -> S3 gbar of kernels without GREG
 };
 
 enum { MODE_STEP = 0, MODE_MOMENTS = 1 };
@@ -583,7 +583,10 @@ __device__ __forceinline__ float phi_div_u(float phi, const float* xs, const flo
 // FF: the forced order-parameter LBE (f_form 1; FP32 storage only).
 // XW: the x axis may have walls; false (a periodic x axis) compiles out the ghost columns and the
 // column wall tests of the gathers.
-template <int NT, int MODE, int ST, bool SD, bool FF = false, bool XW = true>
+// GREG: the pulled gbar of a row stays in registers from S2 to the next iteration's S3 (c3: 41.6
+// -> 40.8 us at 149 registers); without it, in a shared-memory slot (the batch kernel, which
+// holds 128 registers and would spill).
+template <int NT, int MODE, int ST, bool SD, bool FF = false, bool XW = true, bool GREG = true>
 __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const MomentOut mo, int strip, int seg,
                                       Smem<NT>& sm) {
   const int t = threadIdx.x;
@@ -704,6 +707,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
   if (s0_active(ya - 3)) fetch_f(ya - 3, Checked{});
 
   Rec cur{}, prev{};
+  float gcur[Q], gprev[Q];                   // pulled gbar of the S2 row, then of the S3 row
   int fslot = 0;                             // (a - ya + 3) mod RING_F: ring slot of row a
   // One row iteration.  Inner iterations (every stage active, every touched row interior) drop
   // all row tests; the fetches then run for every thread (their columns are always in range).
@@ -796,7 +800,10 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         } else {
           if (in_w0 && (IN || r >= ya)) {
 #pragma unroll
-            for (int k = 0; k < Q; ++k) sm.g[r & 1][k][t] = gb[k];
+            for (int k = 0; k < Q; ++k) {
+              if constexpr (GREG) gcur[k] = gb[k];
+              else sm.g[r & 1][k][t] = gb[k];
+            }
           }
           s2_record(P, s2, ph, m0[0], sdef, cur);
           if constexpr (FF) {
@@ -835,7 +842,7 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
           f[2 * k + 2] = v.y;
         }
 #pragma unroll
-        for (int k = 0; k < Q; ++k) gb[k] = sm.g[r & 1][k][t];
+        for (int k = 0; k < Q; ++k) gb[k] = GREG ? gprev[k] : sm.g[r & 1][k][t];
         if (SD) {
           // div(rho u) of this step, for the next step's mass defect; rho from the phi rings as in S2
           const float* xs_ = uring + (IN ? uslot(a - 6) : uslot_ck(a - 6)) + t;
@@ -862,6 +869,10 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
       }
     }
     prev = cur;
+    if constexpr (GREG) {
+#pragma unroll
+      for (int k = 0; k < Q; ++k) gprev[k] = gcur[k];
+    }
     fslot = fslot == RING_F - 1 ? 0 : fslot + 1;
   };
 
