@@ -27,7 +27,9 @@ struct SimDesc {
 // only that tile body is compiled in.  One function holding both bodies (each for three
 // storages) did not fit 128 registers: it spilled 1.2 KB per thread, and a batch of s_form 1
 // members ran at 14.5 GLUPS against 18.8 with the instances split.
-template <int NT, bool SD>
+// XW: some member may have walls on x; false compiles out the ghost columns and column wall tests
+// (every member periodic in x).
+template <int NT, bool SD, bool XW>
 __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restrict__ sims, const int4* __restrict__ work,
                                               int n_work, int parity) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -41,9 +43,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
     g.dst = odd ? const_cast<void*>(d.buf0) : d.buf1;
     // members may differ in storage; the branch is uniform per tile
     switch (g.storage) {
-      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
-      default: run_tile<NT, MODE_STEP, ST_FP32, SD, false, true, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_FP16: run_tile<NT, MODE_STEP, ST_FP16, SD, false, XW, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      case ST_BF16: run_tile<NT, MODE_STEP, ST_BF16, SD, false, XW, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
+      default: run_tile<NT, MODE_STEP, ST_FP32, SD, false, XW, false>(d.P, g, MomentOut{}, it.y, it.z, sm); break;
     }
     __syncthreads();  // shared rings are reused by the next tile
   }
@@ -53,26 +55,34 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_batch(const SimDesc* __restric
 
 using namespace lbm;
 
-template <bool SD>
+template <bool SD, bool XW>
 static cudaError_t set_batch_attr_sd(int nt) {
   switch (nt) {
-    case 64: return cudaFuncSetAttribute(k_batch<64, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<64>));
-    case 256: return cudaFuncSetAttribute(k_batch<256, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
-    default: return cudaFuncSetAttribute(k_batch<128, SD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<128>));
+    case 64: return cudaFuncSetAttribute(k_batch<64, SD, XW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<64>));
+    case 256: return cudaFuncSetAttribute(k_batch<256, SD, XW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<256>));
+    default: return cudaFuncSetAttribute(k_batch<128, SD, XW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem<128>));
   }
 }
 
-static cudaError_t set_batch_attr(int nt, bool sd) { return sd ? set_batch_attr_sd<true>(nt) : set_batch_attr_sd<false>(nt); }
+static cudaError_t set_batch_attr(int nt, bool sd, bool xw) {
+  if (sd) return xw ? set_batch_attr_sd<true, true>(nt) : set_batch_attr_sd<true, false>(nt);
+  return xw ? set_batch_attr_sd<false, true>(nt) : set_batch_attr_sd<false, false>(nt);
+}
 
-template <bool SD>
-static int batch_occupancy_sd(int nt) {
+template <bool SD, bool XW>
+static int batch_occupancy_t(int nt) {
   int occ = 0;
   switch (nt) {
-    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<64, SD>, 64, sizeof(Smem<64>)); break;
-    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<256, SD>, 256, sizeof(Smem<256>)); break;
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<128, SD>, 128, sizeof(Smem<128>)); break;
+    case 64: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<64, SD, XW>, 64, sizeof(Smem<64>)); break;
+    case 256: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<256, SD, XW>, 256, sizeof(Smem<256>)); break;
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<128, SD, XW>, 128, sizeof(Smem<128>)); break;
   }
   return occ;
+}
+
+template <bool SD>
+static int batch_occupancy_sd(int nt, bool xw) {
+  return xw ? batch_occupancy_t<SD, true>(nt) : batch_occupancy_t<SD, false>(nt);
 }
 
 constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even: parity-neutral)
@@ -93,6 +103,7 @@ struct lbm_batch {
   int n_plain = 0;                     // work[0, n_plain): members without the direct mass defect
   int grid_plain = 0, grid_sd = 0;     // persistent grid of each launch
   int flip = 0;                        // parity offset of every member since the last rebuild
+  bool xwall = true;                   // some member has walls on x (the general kernel form)
   std::map<int, cudaGraphExec_t> graphs;  // flip -> executable graph of GRAPH_STEPS steps
 };
 
@@ -113,8 +124,10 @@ static int rebuild(lbm_batch* b) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  set_batch_attr(b->nt, false);   // the occupancy query needs the shared-memory size admitted
-  const int slots = sms * std::max(batch_occupancy_sd<false>(b->nt), 1);
+  b->xwall = false;
+  for (int m : members) b->xwall = b->xwall || b->slots[m]->params.bc_x == LBM_WALL;
+  set_batch_attr(b->nt, false, b->xwall);   // the occupancy query needs the shared-memory size admitted
+  const int slots = sms * std::max(batch_occupancy_sd<false>(b->nt, b->xwall), 1);
   for (size_t m = 0; m < members.size(); ++m) {
     lbm_sim* s = b->slots[members[m]];
     SimDesc d{};
@@ -179,12 +192,12 @@ static int rebuild(lbm_batch* b) {
   b->n_plain = n_plain;
   b->grid_plain = b->grid_sd = 0;
   if (b->n_plain > 0) {
-    if ((e = set_batch_attr(b->nt, false)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
-    b->grid_plain = std::max(1, std::min(b->n_plain, sms * std::max(batch_occupancy_sd<false>(b->nt), 1)));
+    if ((e = set_batch_attr(b->nt, false, b->xwall)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+    b->grid_plain = std::max(1, std::min(b->n_plain, sms * std::max(batch_occupancy_sd<false>(b->nt, b->xwall), 1)));
   }
   if (b->n_work > b->n_plain) {
-    if ((e = set_batch_attr(b->nt, true)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
-    b->grid_sd = std::max(1, std::min(b->n_work - b->n_plain, sms * std::max(batch_occupancy_sd<true>(b->nt), 1)));
+    if ((e = set_batch_attr(b->nt, true, b->xwall)) != cudaSuccess) return cuda_fail(e, "batch kernel attribute");
+    b->grid_sd = std::max(1, std::min(b->n_work - b->n_plain, sms * std::max(batch_occupancy_sd<true>(b->nt, b->xwall), 1)));
   }
   b->flip = 0;
   drop_graphs(b);
@@ -192,13 +205,19 @@ static int rebuild(lbm_batch* b) {
   return LBM_OK;
 }
 
+template <bool SD, bool XW>
+static void launch_part_t(lbm_batch* b, const int4* work, int n, int grid, int parity, cudaStream_t st) {
+  switch (b->nt) {
+    case 64: k_batch<64, SD, XW><<<grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, work, n, parity); break;
+    case 256: k_batch<256, SD, XW><<<grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, work, n, parity); break;
+    default: k_batch<128, SD, XW><<<grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, work, n, parity); break;
+  }
+}
+
 template <bool SD>
 static void launch_part(lbm_batch* b, const int4* work, int n, int grid, int parity, cudaStream_t st) {
-  switch (b->nt) {
-    case 64: k_batch<64, SD><<<grid, 64, sizeof(Smem<64>), st>>>(b->d_sims, work, n, parity); break;
-    case 256: k_batch<256, SD><<<grid, 256, sizeof(Smem<256>), st>>>(b->d_sims, work, n, parity); break;
-    default: k_batch<128, SD><<<grid, 128, sizeof(Smem<128>), st>>>(b->d_sims, work, n, parity); break;
-  }
+  if (b->xwall) launch_part_t<SD, true>(b, work, n, grid, parity, st);
+  else launch_part_t<SD, false>(b, work, n, grid, parity, st);
 }
 
 // One time step of every member: the two launches touch disjoint members.
