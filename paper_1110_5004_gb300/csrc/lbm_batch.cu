@@ -64,8 +64,10 @@ static cudaError_t set_batch_attr_sd(int nt) {
   }
 }
 
+// Members with the direct mass defect always run the general form: its periodic form does not
+// fit 128 registers (it spilled 36 bytes per thread).
 static cudaError_t set_batch_attr(int nt, bool sd, bool xw) {
-  if (sd) return xw ? set_batch_attr_sd<true, true>(nt) : set_batch_attr_sd<true, false>(nt);
+  if (sd) return set_batch_attr_sd<true, true>(nt);
   return xw ? set_batch_attr_sd<false, true>(nt) : set_batch_attr_sd<false, false>(nt);
 }
 
@@ -82,7 +84,8 @@ static int batch_occupancy_t(int nt) {
 
 template <bool SD>
 static int batch_occupancy_sd(int nt, bool xw) {
-  return xw ? batch_occupancy_t<SD, true>(nt) : batch_occupancy_t<SD, false>(nt);
+  if constexpr (SD) return batch_occupancy_t<SD, true>(nt);
+  else return xw ? batch_occupancy_t<SD, true>(nt) : batch_occupancy_t<SD, false>(nt);
 }
 
 constexpr int GRAPH_STEPS = 16;        // steps per captured graph (even: parity-neutral)
@@ -216,8 +219,12 @@ static void launch_part_t(lbm_batch* b, const int4* work, int n, int grid, int p
 
 template <bool SD>
 static void launch_part(lbm_batch* b, const int4* work, int n, int grid, int parity, cudaStream_t st) {
-  if (b->xwall) launch_part_t<SD, true>(b, work, n, grid, parity, st);
-  else launch_part_t<SD, false>(b, work, n, grid, parity, st);
+  if constexpr (SD) {
+    launch_part_t<SD, true>(b, work, n, grid, parity, st);
+  } else {
+    if (b->xwall) launch_part_t<SD, true>(b, work, n, grid, parity, st);
+    else launch_part_t<SD, false>(b, work, n, grid, parity, st);
+  }
 }
 
 // One time step of every member: the two launches touch disjoint members.

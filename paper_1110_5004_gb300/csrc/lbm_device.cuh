@@ -229,24 +229,40 @@ __device__ __forceinline__ unsigned int ld_raw(const void* __restrict__ base, in
   return COH ? __ldcg(q) : __ldg(q);
 }
 
+// Decoded populations stay in their storage scale: a 16-bit plane (a > 0) holds the population
+// times a power of two (4096 for FP16, 1 for BF16), and the step carries that scale through its
+// linear arithmetic instead of multiplying every value: the sums of S0 and S2 are unscaled once
+// per cell, the collision's per-cell constants are scaled once.  Scaling by a power of two is
+// exact, so every result is bitwise the one of unscaled arithmetic.
 template <int ST>
-__device__ __forceinline__ float dec_pop(unsigned int raw, int a, float inv_scale) {
+__device__ __forceinline__ float dec_pop(unsigned int raw, int a) {
   if (ST == ST_FP32 || a == 0) return __uint_as_float(raw);
   const unsigned short r16 = static_cast<unsigned short>(raw);
-  const float v = ST == ST_FP16 ? __half2float(__ushort_as_half(r16)) : __bfloat162float(__ushort_as_bfloat16(r16));
-  return __fmul_rn(v, inv_scale);   // never contracted: identical rounding in every kernel
+  return ST == ST_FP16 ? __half2float(__ushort_as_half(r16)) : __bfloat162float(__ushort_as_bfloat16(r16));
 }
 
+// Store population a given in storage scale (16-bit planes) or as is (FP32, the rest plane).
 template <int ST>
-__device__ __forceinline__ void st_pop(void* __restrict__ base, int a, CellB c, float v, float scale) {
+__device__ __forceinline__ void st_pop_scaled(void* __restrict__ base, int a, CellB c, float sv) {
   char* p = static_cast<char*>(base) + plane_off<ST>(a);
   if (ST == ST_FP32 || a == 0) {
-    *reinterpret_cast<float*>(p + c.b4) = v;
+    *reinterpret_cast<float*>(p + c.b4) = sv;
   } else {
-    const float sv = __fmul_rn(v, scale);
     *reinterpret_cast<unsigned short*>(p + c.b2) = ST == ST_FP16 ? __half_as_ushort(__float2half_rn(sv))
                                                                  : __bfloat16_as_ushort(__float2bfloat16_rn(sv));
   }
+}
+
+// Store population a given unscaled (the initial state).
+template <int ST>
+__device__ __forceinline__ void st_pop(void* __restrict__ base, int a, CellB c, float v, float scale) {
+  st_pop_scaled<ST>(base, a, c, (ST == ST_FP32 || a == 0) ? v : __fmul_rn(v, scale));
+}
+
+// Multiply by a storage scale only where populations are stored in 16 bits.
+template <int ST>
+__device__ __forceinline__ float to_scale(float v, float scale) {
+  return ST == ST_FP32 ? v : __fmul_rn(v, scale);
 }
 
 // Pull the 9 pre-collision populations of one distribution (planes starting at `src`), as stored
@@ -373,7 +389,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
   const float gmw = fmul(w, poly);
   if (PART != COLLIDE_F) {
     const float S = fmad(gmw, t2, t1w);
-    st_pop<ST>(g.dst, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))), g.sg);
+    st_pop_scaled<ST>(g.dst, Q + A, cell, fmad(k.src_g, S, fmad(k.ogr3, gmw, fmad(k.keep_g, gb[A], k.A[C]))));
   }
   if (A > 0 && PART != COLLIDE_G) {
     float ofeq;
@@ -386,7 +402,7 @@ __device__ __forceinline__ void collide_dir(const CollideC& k, const float f[Q],
     }
     fsum = fadd(fsum, f[A]);
     ofeqsum = fadd(ofeqsum, ofeq);
-    st_pop<ST>(g.dst, A, cell, fmad(k.keep_f, f[A], ofeq), g.sf);
+    st_pop_scaled<ST>(g.dst, A, cell, fmad(k.keep_f, f[A], ofeq));
   }
 }
 
@@ -417,20 +433,21 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   k.wuF[0] = fmul(-4.0f / 9.0f, uF);
   k.wuF[1] = fmul(-1.0f / 9.0f, uF);
   k.wuF[2] = fmul(-1.0f / 36.0f, uF);
+  // terms added to a stored (16-bit: scaled) population carry the storage scale
   const float ogp = fmul(r.og, p);
-  k.A[0] = fmul(4.0f / 9.0f, ogp);
-  k.A[1] = fmul(1.0f / 9.0f, ogp);
-  k.A[2] = fmul(1.0f / 36.0f, ogp);
-  k.ogr3 = r.ogr3;
+  k.A[0] = to_scale<ST>(fmul(4.0f / 9.0f, ogp), g.sg);
+  k.A[1] = to_scale<ST>(fmul(1.0f / 9.0f, ogp), g.sg);
+  k.A[2] = to_scale<ST>(fmul(1.0f / 36.0f, ogp), g.sg);
+  k.ogr3 = to_scale<ST>(r.ogr3, g.sg);
   k.keep_g = fsub(1.0f, r.og);
-  k.src_g = fmad(-0.5f, r.og, 1.0f);
+  k.src_g = to_scale<ST>(fmad(-0.5f, r.og, 1.0f), g.sg);
   k.keep_f = P.keep_f;
   const float ofg = fadd(fmul(P.of3gf, r.mu), phiD), ofp = fmul(P.omega_f, r.phi);
   k.ofwg[0] = k.ofwp[0] = 0.0f;
-  k.ofwg[1] = fmul(1.0f / 9.0f, ofg);
-  k.ofwg[2] = fmul(1.0f / 36.0f, ofg);
-  k.ofwp[1] = fmul(1.0f / 9.0f, ofp);
-  k.ofwp[2] = fmul(1.0f / 36.0f, ofp);
+  k.ofwg[1] = to_scale<ST>(fmul(1.0f / 9.0f, ofg), g.sf);
+  k.ofwg[2] = to_scale<ST>(fmul(1.0f / 36.0f, ofg), g.sf);
+  k.ofwp[1] = to_scale<ST>(fmul(1.0f / 9.0f, ofp), g.sf);
+  k.ofwp[2] = to_scale<ST>(fmul(1.0f / 36.0f, ofp), g.sf);
   if constexpr (FF) {
     const float hx = fmul(P.hf12, r.gx12), hy = fmul(P.hf12, r.gy12);
     k.hgx = hx;
@@ -459,6 +476,8 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
   // f*_0 = phi_hi + [(phi_lo - sum f_a) + (omega_f sum f_a - sum (omega_f f^eq_a + w_a phiD)) + phiD].
   // Only small terms are rounded before the one error-free sum with the O(1) high word.
   if (PART == COLLIDE_G) return;
+  fsum = to_scale<ST>(fsum, g.isf);          // back from the storage scale (exact)
+  ofeqsum = to_scale<ST>(ofeqsum, g.isf);
   float hi, lo;
   if constexpr (FF) {
     // the forced form changes phi by theta_M lap mu (+ phiD) in the collision
@@ -481,9 +500,11 @@ __device__ __forceinline__ void collide_store(const Phys& P, const Rec& r, float
 // west and east neighbours.
 
 // S0: phi = sum_a f_a as an unevaluated pair hi + lo (fp[0..8] f_0..f_8, fp[9] f_0lo).
-__device__ __forceinline__ void phi_pair(const float fp[NF], float& hi, float& lo) {
-  const float small =
-      fadd(fp[Q], fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8]))));
+// fp[1..8] in storage scale (isf: its inverse).
+template <int ST>
+__device__ __forceinline__ void phi_pair(const float fp[NF], float isf, float& hi, float& lo) {
+  const float s8 = fadd(fadd(fadd(fp[1], fp[2]), fadd(fp[3], fp[4])), fadd(fadd(fp[5], fp[6]), fadd(fp[7], fp[8])));
+  const float small = fadd(fp[Q], to_scale<ST>(s8, isf));
   two_sum(fp[0], small, hi, lo);
 }
 
@@ -514,8 +535,10 @@ __device__ __forceinline__ float lap6_of(const float* s, const float* c, const f
 struct S2Out {
   float rho, cl, fsx, fsy, gy, rrho, ux, uy, rx, ry, p;
 };
+// gb[] in storage scale (isg: its inverse).
+template <int ST>
 __device__ __forceinline__ S2Out s2_cell(const Phys& P, float ph, float gphx, float gphy, float gmx, float gmy,
-                                         float mu0, float sdef, const float gb[Q]) {
+                                         float mu0, float sdef, const float gb[Q], float isg) {
   S2Out o;
   o.cl = __saturatef(fmad(ph, P.inv_2phistar, 0.5f));   // clamp((phi + phi*) / (2 phi*))
   o.rho = fmad(o.cl, P.drho, P.rho_B);
@@ -533,9 +556,9 @@ __device__ __forceinline__ S2Out s2_cell(const Phys& P, float ph, float gphx, fl
   const float s24 = fadd(gb[2], gb[4]), d24 = fsub(gb[2], gb[4]);
   const float s57 = fadd(gb[5], gb[7]), d57 = fsub(gb[5], gb[7]);
   const float s68 = fadd(gb[6], gb[8]), d86 = fsub(gb[8], gb[6]);
-  const float m0g = fadd(fadd(fadd(gb[0], s13), fadd(s24, s57)), s68);
-  const float jx = fadd(fadd(d13, d57), d86);
-  const float jy = fsub(fadd(d24, d57), d86);
+  const float m0g = to_scale<ST>(fadd(fadd(fadd(gb[0], s13), fadd(s24, s57)), s68), isg);
+  const float jx = to_scale<ST>(fadd(fadd(d13, d57), d86), isg);
+  const float jy = to_scale<ST>(fsub(fadd(d24, d57), d86), isg);
   o.rrho = __fdividef(1.0f, o.rho);
   const float rden = P.remove_Fa ? __fdividef(1.0f, fmad(-0.5f, sdef, o.rho)) : o.rrho;
   o.ux = fmul(fmad(3.0f, jx, fmul(0.5f, o.fsx)), rden);
@@ -721,10 +744,10 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
     if (IN ? in_w3 : s0_active(a)) {
       float fp[NF];
 #pragma unroll
-      for (int k = 0; k < Q; ++k) fp[k] = dec_pop<ST>(fpr[k], k, g.isf);
+      for (int k = 0; k < Q; ++k) fp[k] = dec_pop<ST>(fpr[k], k);
       fp[Q] = __uint_as_float(fpr[Q]);
       float hi, lo;
-      phi_pair(fp, hi, lo);
+      phi_pair<ST>(fp, g.isf, hi, lo);
       put(o0, a, R_PHI_HI, hi, CK{});
       put(o0, a, R_PHI_LO, lo, CK{});
       if (MODE == MODE_STEP && in_w0 && (IN || a >= ya)) {
@@ -775,8 +798,8 @@ __device__ __forceinline__ void run_tile(const Phys P, const Grid g, const Momen
         }
         float gb[Q];
 #pragma unroll
-        for (int k = 0; k < Q; ++k) gb[k] = dec_pop<ST>(gpr[k], Q + k, g.isg);
-        const S2Out s2 = s2_cell(P, ph, gphx, gphy, gmx, gmy, m0[0], sdef, gb);
+        for (int k = 0; k < Q; ++k) gb[k] = dec_pop<ST>(gpr[k], Q + k);
+        const S2Out s2 = s2_cell<ST>(P, ph, gphx, gphy, gmx, gmy, m0[0], sdef, gb, g.isg);
         const float rho = s2.rho, ux = s2.ux, uy = s2.uy, p = s2.p;
         put(o4, r, R_P, p, CK{});
         if (MODE == MODE_STEP && (P.ch_conv || SD)) put_u(r, ux, uy, CK{});

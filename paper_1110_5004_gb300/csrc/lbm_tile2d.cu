@@ -98,10 +98,10 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
     if (k >= FW * FH || !real(x, y)) continue;
     float fp[NF];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) fp[a] = dec_pop<ST>(f0raw[c][a], a, g.isf);
+    for (int a = 0; a < Q; ++a) fp[a] = dec_pop<ST>(f0raw[c][a], a);
     fp[Q] = __uint_as_float(f0raw[c][Q]);
     float hi, lo;
-    phi_pair(fp, hi, lo);
+    phi_pair<ST>(fp, g.isf, hi, lo);
     put(sm.hi, i, j, x, y, hi);
     put(sm.lo, i, j, x, y, lo);
     const int ti = i - 3, tj = j - 3;
@@ -132,8 +132,8 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
     const float sdef = P.remove_Fa ? fmul(P.s_coef6, lap6_of(&sm.mu[j - 1][i], &sm.mu[j][i], &sm.mu[j + 1][i])) : 0.0f;
     float gb[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) gb[a] = dec_pop<ST>(g2raw[c][a], Q + a, g.isg);
-    const S2Out s2 = s2_cell(P, ph, gphx, gphy, gmx, gmy, sm.mu[j][i], sdef, gb);
+    for (int a = 0; a < Q; ++a) gb[a] = dec_pop<ST>(g2raw[c][a], Q + a);
+    const S2Out s2 = s2_cell<ST>(P, ph, gphx, gphy, gmx, gmy, sm.mu[j][i], sdef, gb, g.isg);
     put(sm.p, i, j, x, y, s2.p);
     if (P.ch_conv) {
       put(sm.ux, i, j, x, y, s2.ux);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void tile2d_step(const Phys& P, const Grid& g, int ti
                                      : 0.0f;
         f[0] = 0.0f;   // unused: f_0 follows from the phi pair
 #pragma unroll
-        for (int a = 1; a < Q; ++a) f[a] = dec_pop<ST>(sm.f3[a - 1][tj][ti], a, g.isf);
+        for (int a = 1; a < Q; ++a) f[a] = dec_pop<ST>(sm.f3[a - 1][tj][ti], a);
 #pragma unroll
         for (int a = 0; a < Q; ++a) gb[a] = 0.0f;   // unused by the f collision
         collide_store<ST, false, COLLIDE_F>(P, r, 0.0f, 0.0f, 0.0f, sm.hi[j][i], sm.lo[j][i], phiD, f, gb, g, cell);
