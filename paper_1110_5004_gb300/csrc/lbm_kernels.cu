@@ -29,11 +29,12 @@ __global__ void __launch_bounds__(NT, NT == 128 ? 3 : 512 / NT) k_tiles(Phys P, 
 
 static int n_tiles(const Grid& g) { return g.n_strips * ((g.ny + g.seg_h - 1) / g.seg_h); }
 
-// Dynamic shared memory of a step CTA.  The periodic-x form (XW false) needs fewer registers
-// (128 against 141 for 128 threads) and would fit 4 CTAs per SM where the general form fits 3;
-// it is held to the general form's count, for which the tile heights are sized (one wave) and
-// which measured faster (c3 42.8 us on 128 x 20 at 3 per SM against 45.6 us on 128 x 15 at 4),
-// by asking for just more shared memory than one more CTA would leave room for.
+// Dynamic shared memory of a row-march CTA (step or moments).  The periodic-x form (XW false)
+// can need fewer registers than the general form and then fit more CTAs per SM; it is held to
+// the general form's count, for which the tile heights are sized (one wave) and which measured
+// faster (c3 42.8 us on 128 x 20 at 3 per SM against 45.6 us on 128 x 15 at 4, when the form
+// took 128 registers), by asking for just more shared memory than one more CTA would leave room
+// for.
 template <int NT, bool XW>
 static int step_smem_bytes() {
   int smem = (int)sizeof(Smem<NT>);
@@ -56,7 +57,7 @@ template <int NT, int MODE, int ST, bool SD, bool FF, bool XW = true>
 static cudaError_t launch_sd(const Phys& P, const Grid& g, const MomentOut& mo, cudaStream_t st) {
   static int smem = 0;   // one GPU per process
   if (smem == 0) {
-    const int want = MODE == MODE_STEP ? step_smem_bytes<NT, XW>() : (int)sizeof(Smem<NT>);
+    const int want = step_smem_bytes<NT, XW>();
     cudaError_t e = cudaFuncSetAttribute(k_tiles<NT, MODE, ST, SD, FF, XW>, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
     if (e != cudaSuccess) return e;
     smem = want;
@@ -88,10 +89,8 @@ static cudaError_t launch_nt(const Phys& P, const Grid& g, const MomentOut& mo, 
                         : launch_sd<NT, MODE, ST, false, true>(P, g, mo, st);
   }
   if (P.s_direct) return launch_sd<NT, MODE, ST, true, false>(P, g, mo, st);
-  // the plain step on a periodic x axis compiles out the ghost columns and column wall tests
-  if constexpr (MODE == MODE_STEP) {
-    if (g.bc_x != BC_WALL) return launch_sd<NT, MODE, ST, false, false, false>(P, g, mo, st);
-  }
+  // a periodic x axis compiles out the ghost columns and column wall tests
+  if (g.bc_x != BC_WALL) return launch_sd<NT, MODE, ST, false, false, false>(P, g, mo, st);
   return launch_sd<NT, MODE, ST, false, false>(P, g, mo, st);
 }
 
@@ -166,44 +165,46 @@ __global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
 
 // Post-collision-layout state whose pull gives f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0):
 // plane a at cell z holds the equilibrium of direction a at z + e_a, or, when that link leaves
-// through a wall, the equilibrium of the reversed direction at z itself.
+// through a wall, the equilibrium of the reversed direction at z itself.  Written by pushing:
+// each cell evaluates its own 18 equilibria once and stores direction a at the cell it is pulled
+// from, z - e_a, or, when that lies beyond a wall, as the reversed plane at itself (which the
+// pull's bounce-back reads).  Every (plane, cell) is written exactly once.
 template <int ST>
 __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
-    const float* phi = fields;
-    const float* ux = fields + 2 * g.plane;
-    const float* uy = fields + 3 * g.plane;
-    const float* pp = fields + 4 * g.plane;
-    const float* mu = fields + 5 * (long long)g.plane;
-    const CellB cell = cell_at(y * g.row_bytes, col_bytes<ST>(x));
+    const long long c = (long long)y * g.pitch + x;
+    const float ph = fields[c], u = fields[2 * g.plane + c], v = fields[3 * g.plane + c];
+    const float p = fields[4 * g.plane + c], m = fields[5 * (long long)g.plane + c];
+    const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
+    const float rho = P.rho_B + cl * P.drho;
+    const float uu15 = 1.5f * (u * u + v * v);
+    const CellB self = cell_at(y * g.row_bytes, col_bytes<ST>(x));
   #pragma unroll
     for (int a = 0; a < Q; ++a) {
-      int xw = x + cx(a), yw = y + cy(a);
-      int b = a;
-      bool hit = false;
-      if (xw < 0 || xw >= g.nx) {
-        if (g.bc_x == BC_WALL) hit = true; else xw = wrap(xw, g.nx);
-      }
-      if (yw < 0 || yw >= g.ny) {
-        if (g.bc_y == BC_WALL) hit = true; else yw = wrap(yw, g.ny);
-      }
-      if (hit) {
-        xw = x;
-        yw = y;
-        b = opp(a);
-      }
-      const long long c = (long long)yw * g.pitch + xw;
-      const float ph = phi[c], u = ux[c], v = uy[c], p = pp[c], m = mu[c];
-      const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
-      const float rho = P.rho_B + cl * P.drho;
-      const float uu15 = 1.5f * (u * u + v * v);
-      const float w = wgt(b);
-      const float eu = (float)cx(b) * u + (float)cy(b) * v;
+      const float w = wgt(a);
+      const float eu = (float)cx(a) * u + (float)cy(a) * v;
       const float poly = 3.0f * eu + 4.5f * eu * eu - uu15;
       const float geq = w * p + rho * (1.0f / 3.0f) * (w * poly);
-      if (b == 0) {
+      float feq = 0.0f;
+      if (a > 0) feq = w * (P.f_forced ? ph * (1.0f + poly) : P.three_gamma_f * m + ph * poly);
+      // where direction a's value is pulled from: z = this cell - e_a, or itself across a wall
+      int xz = x - cx(a), yz = y - cy(a), plane = a;
+      bool hit = false;
+      if (xz < 0 || xz >= g.nx) {
+        if (g.bc_x == BC_WALL) hit = true; else xz = wrap(xz, g.nx);
+      }
+      if (yz < 0 || yz >= g.ny) {
+        if (g.bc_y == BC_WALL) hit = true; else yz = wrap(yz, g.ny);
+      }
+      if (hit) {
+        xz = x;
+        yz = y;
+        plane = opp(a);
+      }
+      const CellB z = a == 0 ? self : cell_at(yz * g.row_bytes, col_bytes<ST>(xz));
+      if (a == 0) {
         // f_0^eq = phi - sum_{k>0} f^eq_k, kept as the float pair (hi, lo)
         float rest = 0.0f;
   #pragma unroll
@@ -216,15 +217,15 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
         float hi, lo;
         two_sum(ph, -rest, hi, lo);
         if (ST == ST_FP32) {
-          st_pop<ST>(g.dst, 0, cell, hi, 1.0f);
-          st_pop<ST>(g.dst, PLANE_F0LO, cell, lo, 1.0f);
+          st_pop<ST>(g.dst, 0, self, hi, 1.0f);
+          st_pop<ST>(g.dst, PLANE_F0LO, self, lo, 1.0f);
         } else {
-          st_pop<ST>(g.dst, 0, cell, hi + lo, 1.0f);
+          st_pop<ST>(g.dst, 0, self, hi + lo, 1.0f);
         }
       } else {
-        st_pop<ST>(g.dst, a, cell, w * (P.f_forced ? ph * (1.0f + poly) : P.three_gamma_f * m + ph * poly), g.sf);
+        st_pop<ST>(g.dst, plane, z, feq, g.sf);
       }
-      st_pop<ST>(g.dst, Q + a, cell, geq, g.sg);
+      st_pop<ST>(g.dst, Q + plane, z, geq, g.sg);
     }
   }
 }
