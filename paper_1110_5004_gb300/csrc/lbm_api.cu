@@ -270,7 +270,7 @@ int lbm_init_fields(lbm_sim* s, const float* phi0, const float* ux0, const float
   e = launch_init(s, s->stream);
   if (e == cudaSuccess) e = rearm_resident(s);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields launch");
-  s->launches += s->params.s_form ? 3 : 2;
+  s->launches += s->params.s_form ? 2 : 1;
   s->steps = 0;
   // host inputs must be consumed before return (pageable copies already are; pinned ones not):
   // wait for the copies only, so the initialisation kernels overlap the caller's next launches.
@@ -312,7 +312,7 @@ int lbm_init_fields_packed(lbm_sim* s, const float* fields) {
   e = launch_init(s, s->stream);
   if (e == cudaSuccess) e = rearm_resident(s);
   if (e != cudaSuccess) return cuda_fail(e, "lbm_init_fields_packed launch");
-  s->launches += s->params.s_form ? 3 : 2;
+  s->launches += s->params.s_form ? 2 : 1;
   s->steps = 0;
   if (host && (e = cudaEventSynchronize(s->uploaded)) != cudaSuccess)
     return cuda_fail(e, "lbm_init_fields_packed sync");

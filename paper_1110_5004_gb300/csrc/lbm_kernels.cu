@@ -142,26 +142,8 @@ cudaError_t launch_moments(const Phys& P, const Grid& g, const MomentOut& mo, in
 }
 
 // ------------------------------------------------------------------ initial state
-// fields: [0] phi0, [1] (unused), [2] ux0, [3] uy0, [4] p0, [5] mu0 -- pitched planes.
-
-__global__ void k_init_mu(Phys P, Grid g, float* __restrict__ fields) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= g.nx) return;
-  for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
-    const float* phi = fields;
-    float* mu = fields + 5 * (long long)g.plane;
-    auto at = [&](int dx, int dy) {
-      int xx = x + dx, yy = y + dy;
-      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
-      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
-      return phi[(long long)yy * g.pitch + xx];
-    };
-    const float ph = at(0, 0);
-    const float lap = (4.0f * (at(1, 0) + at(0, 1) + at(-1, 0) + at(0, -1)) +
-                       (at(1, 1) + at(-1, 1) + at(-1, -1) + at(1, -1)) - 20.0f * ph) * (1.0f / 6.0f);
-    mu[(long long)y * g.pitch + x] = P.four_beta * ph * (ph * ph - P.phi_star2) - P.kappa * lap;
-  }
-}
+// fields: [0] phi0, [1] (unused), [2] ux0, [3] uy0, [4] p0 -- pitched planes; mu0 is evaluated
+// where it is used.
 
 // Post-collision-layout state whose pull gives f = f^eq(phi0, mu0, u0), gbar = g^eq(p0, rho0, u0):
 // plane a at cell z holds the equilibrium of direction a at z + e_a, or, when that link leaves
@@ -176,7 +158,17 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
   for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {   // gridDim.y is capped at 65535
     const long long c = (long long)y * g.pitch + x;
     const float ph = fields[c], u = fields[2 * g.plane + c], v = fields[3 * g.plane + c];
-    const float p = fields[4 * g.plane + c], m = fields[5 * (long long)g.plane + c];
+    const float p = fields[4 * g.plane + c];
+    // mu0 = theta'(phi0) - kappa lap(phi0) (Eq. 1); beyond a wall phi is mirrored (zero gradient)
+    auto at = [&](int dx, int dy) {
+      int xx = x + dx, yy = y + dy;
+      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap1(xx, g.nx);
+      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap1(yy, g.ny);
+      return fields[(long long)yy * g.pitch + xx];
+    };
+    const float lap = (4.0f * (at(1, 0) + at(0, 1) + at(-1, 0) + at(0, -1)) +
+                       (at(1, 1) + at(-1, 1) + at(-1, -1) + at(1, -1)) - 20.0f * ph) * (1.0f / 6.0f);
+    const float m = P.four_beta * ph * (ph * ph - P.phi_star2) - P.kappa * lap;
     const float cl = fminf(fmaxf((ph + P.phi_star) * P.inv_2phistar, 0.0f), 1.0f);
     const float rho = P.rho_B + cl * P.drho;
     const float uu15 = 1.5f * (u * u + v * v);
@@ -193,10 +185,10 @@ __global__ void k_init_pop(Phys P, Grid g, const float* __restrict__ fields) {
       int xz = x - cx(a), yz = y - cy(a), plane = a;
       bool hit = false;
       if (xz < 0 || xz >= g.nx) {
-        if (g.bc_x == BC_WALL) hit = true; else xz = wrap(xz, g.nx);
+        if (g.bc_x == BC_WALL) hit = true; else xz = wrap1(xz, g.nx);
       }
       if (yz < 0 || yz >= g.ny) {
-        if (g.bc_y == BC_WALL) hit = true; else yz = wrap(yz, g.ny);
+        if (g.bc_y == BC_WALL) hit = true; else yz = wrap1(yz, g.ny);
       }
       if (hit) {
         xz = x;
@@ -240,8 +232,8 @@ __global__ void k_init_sdef(Phys P, Grid g, const float* __restrict__ fields) {
     const float* uy = fields + 3 * g.plane;
     auto idx = [&](int dx, int dy) {
       int xx = x + dx, yy = y + dy;
-      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap(xx, g.nx);
-      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap(yy, g.ny);
+      xx = g.bc_x == BC_WALL ? mirror(xx, g.nx) : wrap1(xx, g.nx);
+      yy = g.bc_y == BC_WALL ? mirror(yy, g.ny) : wrap1(yy, g.ny);
       return (long long)yy * g.pitch + xx;
     };
     auto rho = [&](long long i) { return fmad(__saturatef(fmad(phi[i], P.inv_2phistar, 0.5f)), P.drho, P.rho_B); };
@@ -259,9 +251,6 @@ __global__ void k_init_sdef(Phys P, Grid g, const float* __restrict__ fields) {
 cudaError_t launch_init(const lbm_sim* s, cudaStream_t st) {
   Grid g = make_grid(s, nullptr, s->buf[s->cur]);
   dim3 blk(128), grd((s->nx + 127) / 128, s->ny < 65535 ? s->ny : 65535);
-  k_init_mu<<<grd, blk, 0, st>>>(s->phys, g, s->fields);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   switch (g.storage) {
     case ST_FP16: k_init_pop<ST_FP16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
     case ST_BF16: k_init_pop<ST_BF16><<<grd, blk, 0, st>>>(s->phys, g, s->fields); break;
