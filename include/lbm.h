@@ -49,7 +49,8 @@ extern "C" {
 /* population storage */
 #define LBM_FP32 0     /* 4-byte populations */
 #define LBM_FP16_DEV 1 /* 2-byte fp16 deviations from the lattice-weight baseline, FP32 math */
-#define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math */
+#define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math; stored by stochastic rounding
+                          (unbiased, deterministic for a given value and place) */
 
 /* step kernel (lbm_set_kernel) */
 #define LBM_KERNEL_AUTO 0  /* the 2-D tile kernel where it applies on grids of at most 262144
