@@ -206,20 +206,26 @@ __global__ void __launch_bounds__(NT) k_tile2d(Phys P, Grid g, int tiles_x) {
 // few tiles then spreads evenly over the SMs instead of piling several CTAs onto some while
 // others idle.  0 when the device attributes cannot be read.
 static int smem_for_cap(int need, int cap) {
-  static int per_sm = -1, reserved = 0, optin = 0;
-  if (per_sm < 0) {
+  struct Attrs {
+    int per_sm = 0, reserved = 0, optin = 0;
+  };
+  // read once per process (one GPU per process), thread-safely: host threads may step
+  // simulations concurrently
+  static const Attrs at = [] {
+    Attrs a;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaDeviceGetAttribute(&a.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&a.reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&a.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
       cudaGetLastError();
-      per_sm = 0;
+      a = Attrs{};
     }
-  }
-  if (per_sm <= 0) return need;
-  const int want = (per_sm / (cap + 1) - reserved + 16 + 15) / 16 * 16;   // cap + 1 no longer fit
-  if (want <= need || want > optin || cap * (want + reserved) > per_sm) return need;
+    return a;
+  }();
+  if (at.per_sm <= 0) return need;
+  const int want = (at.per_sm / (cap + 1) - at.reserved + 16 + 15) / 16 * 16;   // cap + 1 no longer fit
+  if (want <= need || want > at.optin || cap * (want + at.reserved) > at.per_sm) return need;
   return want;
 }
 
