@@ -251,7 +251,7 @@ def batch_leg(args, lbm, torch):
     out["accuracy"] = {"fp32": "FP32 parity with the FP64 oracle (1e-5)",
                        "fp16": "within the reduced-storage bound (phi 1e-3; drift and centroid velocity 0.5 %)",
                        "bf16": "within the reduced-storage bound (stochastic rounding to BF16; falling drop "
-                               "0.1 % in centroid velocity, 3.6e-4 in phi)"}
+                               "0.05 % in centroid velocity, 3.3e-4 in phi)"}
     out["finite_note"] = ("members at density ratios 100 and 1000 leave the finite range under this "
                           "scheme; mlups_finite counts only the members finite after the run")
     return out

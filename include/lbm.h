@@ -49,7 +49,7 @@ extern "C" {
 /* population storage */
 #define LBM_FP32 0     /* 4-byte populations */
 #define LBM_FP16_DEV 1 /* 2-byte fp16 deviations from the lattice-weight baseline, FP32 math */
-#define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math; stored by stochastic rounding
+#define LBM_BF16_DEV 2 /* 2-byte bf16 deviations, FP32 math; gbar stored by stochastic rounding
                           (unbiased, deterministic for a given value and place) */
 
 /* step kernel (lbm_set_kernel) */

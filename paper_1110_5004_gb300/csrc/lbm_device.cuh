@@ -244,8 +244,10 @@ __device__ __forceinline__ float dec_pop(unsigned int raw, int a) {
 // BF16 bits of v by stochastic rounding: a pseudo-random 16-bit offset is added to the 16 bits
 // that truncation drops, so v rounds away from zero with probability equal to the dropped
 // fraction and the rounding error has zero mean.  Round-to-nearest at BF16's 8-bit significand
-// biases populations that change little from step to step the same way every step, which
-// drifted a falling drop's centroid velocity by 3.6 %; unbiased rounding keeps it within 0.05 %.
+// biases the gbar populations, which change little from step to step, the same way every step:
+// a falling drop's centroid velocity drifted by 3.6 %.  Unbiased rounding of the gbar planes
+// keeps it within 0.05 %; the f planes round to nearest (rounding them stochastically as well
+// gained nothing, and rounding only them left the 3.6 %).
 // The offset is a hash of the value's own bits and its storage address, so every kernel rounds a
 // given value at a given place alike and runs stay deterministic.  NaN and infinity keep round-to-nearest, so a diverged state stays
 // non-finite.
@@ -265,9 +267,11 @@ __device__ __forceinline__ void st_pop_scaled(void* __restrict__ base, int a, Ce
     *reinterpret_cast<float*>(p + c.b4) = sv;
   } else if (ST == ST_FP16) {
     *reinterpret_cast<unsigned short*>(p + c.b2) = __half_as_ushort(__float2half_rn(sv));
-  } else {
+  } else if (a >= Q) {   // gbar: stochastic rounding (see bf16_stochastic)
     *reinterpret_cast<unsigned short*>(p + c.b2) =
         bf16_stochastic(sv, static_cast<unsigned int>(c.b2 + plane_off<ST>(a)));
+  } else {                // f: round to nearest meets the bound
+    *reinterpret_cast<unsigned short*>(p + c.b2) = __bfloat16_as_ushort(__float2bfloat16_rn(sv));
   }
 }
 
