@@ -25,7 +25,10 @@
  *     passes in.  Pointers to fields may be host or device memory (detected per call).
  *   - Work is queued on the CUDA stream given at creation (NULL = legacy default stream).
  *     lbm_step is asynchronous; lbm_moments and lbm_diagnostics synchronise that stream.
- *   - One simulation must not be used from two host threads at once.
+ *   - One simulation must not be used from two host threads at once; different simulations
+ *     may be stepped from different host threads concurrently.
+ *   - One GPU per process: the library measures the device it first runs on (multiprocessor
+ *     count, occupancy, shared-memory limits) once and sizes every later launch by it.
  */
 #ifndef LBM_H
 #define LBM_H
