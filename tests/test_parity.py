@@ -467,9 +467,12 @@ def test_c3_splash_bf16_storage(lbm, tile):
     assert err <= 1e-3, err
 
 
-def test_diverged_state_reports_error_code(lbm):
+@pytest.mark.parametrize("st", [0, 1, 2])
+def test_diverged_state_reports_error_code(lbm, st):
+    """A state that left the finite range is reported in every storage: 16-bit stores keep NaN
+    and infinity non-finite (BF16's stochastic rounding included)."""
     w = W.splash(nx=256, ny=128, D=50)
-    sim = lbm.Sim.from_workload(w)
+    sim = lbm.Sim.from_workload(w, storage=st)
     sim.step(30)
     with pytest.raises(lbm.LBMError) as e:
         sim.diagnostics(raise_on_divergence=True)
